@@ -1,0 +1,423 @@
+#!/usr/bin/env python3
+"""Benchmark of the JK-CALS hot path on one or more GPUs (one process per GPU).
+
+One *step* is one JK-CALS sweep (Alg. 3 repeat loop body) over every submodel
+of the workload: for each mode the concurrent MTTKRP, the per-submodel
+Gram-Hadamard Cholesky solve, zeroing, normalisation and Gram refresh, and the
+per-submodel error after the last mode.  The workload is the fluorescence-
+shaped 300x100x50 tensor, rank 5, all 300 leave-one-out submodels.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision P]
+    python bench.py --impl reference ...   # the FP64 CPU oracle (JK-ALS), host cores
+
+Prints one JSON line (rank 0).  Multi-GPU runs are weak scaling: every rank
+fits its own copy of the workload (submodels are independent; no collective
+on the data path), value = all ranks' submodel-iterations / max rank time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "JK submodel-ALS iters/s + MTTKRP TFLOP/s vs plain FP64, factor rel err ≤1e-6"
+UNIT = "submodel-iters/s"
+WORKLOAD = "fluorescence-shaped 300x100x50 FP32 tensor, R=5, 300 LOO submodels (one sweep per step)"
+PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=50)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--precision", default="fp64")
+    p.add_argument("--e2e-reps", type=int, default=3)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-fp64-compare", action="store_true")
+    p.add_argument("--cpu-worker", action="store_true", help=argparse.SUPPRESS)
+    p.add_argument("--seconds", type=float, default=15.0, help=argparse.SUPPRESS)
+    return p.parse_args()
+
+
+# --------------------------------------------------------------------------- peaks
+
+def load_peaks():
+    try:
+        with open(PEAKS_PATH) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+                "sm_max_mhz": 2070.0}, "fallback"
+
+
+# Nominal ratios of the recipe's dense tensor rates (per GPU): TF32 1.1 PF vs BF16 2.25 PF.
+TF32_PER_BF16 = 1.1 / 2.25
+# FP64 on CUDA cores: 152 SMs x 2 DFMA/clk x 2 flop at the maximum SM clock
+# (the recipe's nominal 1.25 TFLOP/s FP64 at 2070 MHz).
+FP64_FLOP_PER_CLK_PER_SM = 4.0
+NUM_SMS = 152
+
+
+def roofline_peak(precision, peaks):
+    if precision == "fp64":
+        return "alu", NUM_SMS * FP64_FLOP_PER_CLK_PER_SM * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12, \
+            "FP64 CUDA-core peak 152 SM x 4 flop/clk x sm_max_mhz (derived)"
+    bf16 = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
+    if precision == "tf32":
+        return "tensor", bf16 * TF32_PER_BF16, "TF32 = measured BF16 sustained x 1.1/2.25"
+    if precision == "3xtf32":
+        return "tensor", bf16 * TF32_PER_BF16 / 3.0, "3xTF32 = measured BF16 sustained x 1.1/2.25 / 3 passes"
+    if precision == "bf16":
+        return "tensor", bf16, "measured BF16 sustained"
+    if precision == "split_bf16":
+        return "tensor", bf16 / 6.0, "measured BF16 sustained / 6 passes"
+    raise ValueError(precision)
+
+
+# --------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu_index = gpu_index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.gpu_index)],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------- CPU oracle
+
+def cpu_worker(seconds):
+    """Times the FP64 oracle (straightforward JK-ALS, Alg. 2) on a bounded sample of
+    the workload's submodels: whole-block fits of all its sweeps, until ~seconds."""
+    import numpy as np
+    import oracle as O
+    from paper_2112_03985_gb300 import workloads as W
+    w = W.make_config(2)
+    t0 = time.perf_counter()
+    blocks = 0
+    sweeps = w.sweeps
+    for g in range(w.K):
+        O.jk_als(w.T, w.n_hat, w.left_out, w.init, sweeps, blocks=[g])
+        blocks += 1
+        if time.perf_counter() - t0 > seconds:
+            break
+    dt = time.perf_counter() - t0
+    print(json.dumps({"value": blocks * sweeps / dt, "blocks": blocks, "sweeps": sweeps, "seconds": dt,
+                      "numpy": np.__version__}))
+
+
+def run_cpu_baseline(seconds=15.0):
+    cores = os.cpu_count() or 1
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[k] = str(cores)
+    env["CUDA_VISIBLE_DEVICES"] = ""
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-worker", "--seconds", str(seconds)],
+                       capture_output=True, text=True, env=env, timeout=600)
+    if r.returncode != 0:
+        return {"value": None, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": "failed: " + r.stderr[-300:]}
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    return {"value": d["value"], "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{d['blocks']} of 300 submodels fitted separately (JK-ALS, Alg. 2) for all "
+                      f"{d['sweeps']} sweeps on their sliced tensors, FP64 NumPy, BLAS threads={cores}, "
+                      f"{d['seconds']:.1f} s"}
+
+
+def reference_arm(args):
+    """--impl reference: the FP64 oracle on the host cores, one JK-ALS sweep of a
+    bounded sample of submodels per step (rank 0 only)."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import numpy as np
+    import oracle as O
+    from paper_2112_03985_gb300 import workloads as W
+    w = W.make_config(2)
+    B = 24
+    sel = list(range(0, w.K, w.K // B))[:B]
+    state = []
+    for g in sel:
+        D = w.left_out[g]
+        Tg = O.slice_tensor(w.T, w.n_hat, D)
+        U = [O.remove_rows(u, D) if k == w.n_hat else u.copy() for k, u in enumerate(w.init[g])]
+        state.append([Tg, [O.unfold(Tg, n) for n in range(3)], U])
+
+    def step():
+        for st in state:
+            r = O.cp_als(st[0], st[2], 1, unfoldings=st[1])
+            st[2] = r.factors
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = time.perf_counter() - t0
+    cores = os.cpu_count() or 1
+    value = B * args.steps / dt
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "impl": "reference",
+           "config": {"workload": WORKLOAD, "sample_per_step": f"{B} of 300 submodels, one sweep each"},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                            "sample": f"{B} of 300 LOO submodels, one JK-ALS sweep each per step, "
+                                      f"sliced tensors and unfoldings prepared before timing"},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+    del np
+
+
+# --------------------------------------------------------------------------- GPU arm
+
+def source_hash(precision):
+    files = ["jk_mttkrp_f64.cu"] if precision == "fp64" else ["jk_mttkrp_tc.cu"]
+    h = hashlib.sha1()
+    for f in files:
+        p = os.path.join(ROOT, "paper_2112_03985_gb300", "csrc", f)
+        if os.path.exists(p):
+            h.update(open(p, "rb").read())
+    return h.hexdigest()[:12]
+
+
+def measured_traffic(precision):
+    """DRAM bytes per MTTKRP launch from a committed ncu summary, if its kernel
+    source is unchanged since the capture."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        d = json.load(open(p))
+        ent = d[precision]
+        if ent.get("source_sha1") == source_hash(precision):
+            return ent["dram_bytes_per_launch"]
+    except Exception:
+        pass
+    return None
+
+
+def gpu_arm(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_2112_03985_gb300 import api, workloads as W
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if not torch.cuda.is_available():
+        raise RuntimeError("bench.py needs a CUDA device (there is no CPU fallback)")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    peaks, peak_src = load_peaks()
+    w = W.make_config(2)
+    T32 = np.ascontiguousarray(w.T.astype(np.float32))
+    init = api.multi_init(w.init)
+    Td = torch.from_numpy(T32).to(dev)
+    initd = [torch.from_numpy(u).to(dev) for u in init]
+    torch.cuda.synchronize()
+
+    h = api.JKCALS(Td, w.n_hat, w.ranks, w.left_out, initd, precision=args.precision, kernel_timing=True)
+    kps, splits = h.sweep_info()
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    for _ in range(args.warmup):
+        flush.zero_()
+        h.als_sweep_async(1)
+    torch.cuda.synchronize()
+
+    gpu_index = local
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if vis:
+        try:
+            gpu_index = int(vis.split(",")[local])
+        except ValueError:
+            pass
+    sampler = ClockSampler(gpu_index)
+    barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    t0 = time.perf_counter()
+    evs = []
+    mtt_ms = []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        h.als_sweep_async(1)
+        e1.record(stream)
+        mtt_ms.append(h.kernel_times())
+        evs.append((e0, e1))
+    torch.cuda.synchronize()
+    barrier()
+    wall = time.perf_counter() - t0
+    clocks = sampler.stop()
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    dev_s = sum(step_ms) / 1e3
+    t_local = torch.tensor([dev_s, wall], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t_local, op=dist.ReduceOp.MAX)
+    dev_s_max, wall_max = float(t_local[0]), float(t_local[1])
+    value = world * w.K * args.steps / dev_s_max
+
+    # MTTKRP roofline: algorithmic flops 2 C prod(I) per launch (Sec. 3.2 / Sec. 4.2 count)
+    flops_launch = 2.0 * w.C * float(np.prod(w.dims))
+    mt = np.array(mtt_ms)  # steps x N
+    avg_launch_s = mt.mean() / 1e3
+    achieved = flops_launch / avg_launch_s / 1e12
+    bound, peak, peak_note = roofline_peak(args.precision, peaks)
+    roof = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": measured_traffic(args.precision), "kernel": "concurrent MTTKRP",
+            "flops_per_launch": flops_launch, "avg_launch_ms": mt.mean(),
+            "peak_source": f"{peak_note} ({peak_src} MEASURED_PEAKS.json)" if bound != "alu" else peak_note,
+            "mttkrp_share_of_step": float(mt.sum() / sum(step_ms))}
+    losses_final = h.als_sweep(1)
+    U_ours = h.get_factors()
+    h.close()
+
+    # plain FP64 on the same GPU (same workload, same sweep count) for the ratio and error
+    fp64 = None
+    if args.precision != "fp64" and not args.no_fp64_compare:
+        h64 = api.JKCALS(Td, w.n_hat, w.ranks, w.left_out, initd, precision="fp64")
+        n64 = max(3, min(args.steps, 10))
+        h64.als_sweep_async(args.warmup + args.steps - n64)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        tot = 0.0
+        for _ in range(n64):
+            flush.zero_()
+            e0.record(stream)
+            h64.als_sweep_async(1)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            tot += e0.elapsed_time(e1)
+        h64.als_sweep(1)
+        U64 = h64.get_factors()
+        h64.close()
+        offs = np.concatenate([[0], np.cumsum(w.ranks)])
+        err = 0.0
+        for n in range(3):
+            for g in range(w.K):
+                a, b = U_ours[n][:, offs[g]:offs[g + 1]], U64[n][:, offs[g]:offs[g + 1]]
+                err = max(err, float(np.linalg.norm(a - b) / np.linalg.norm(b)))
+        fp64 = {"value": w.K * n64 / (tot / 1e3), "ratio": value / world / (w.K * n64 / (tot / 1e3)),
+                "factor_rel_err_vs_fp64_path": err,
+                "sweeps_compared": args.warmup + args.steps + 1}
+
+    # end to end: one whole job from pinned host buffers through the public API
+    e2e = None
+    if args.e2e_reps > 0:
+        Th = torch.from_numpy(T32).pin_memory()
+        inith = [torch.from_numpy(u).pin_memory() for u in init]
+        outs = [torch.empty((I, w.C), dtype=torch.float64).pin_memory() for I in w.dims]
+        lossh = torch.empty((w.sweeps, w.K), dtype=torch.float64).pin_memory()
+        times = []
+        for _ in range(args.e2e_reps):
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            with api.JKCALS(Th, w.n_hat, w.ranks, w.left_out, inith, precision=args.precision,
+                            stream=stream.cuda_stream) as he:
+                he.als_sweep(w.sweeps, losses=lossh)
+                he.get_factors_into(outs)
+            times.append(time.perf_counter() - t)
+        tj = statistics.median(times)
+        h2d = T32.nbytes + sum(u.nbytes for u in init)
+        d2h = lossh.numel() * 8 + sum(o.numel() * 8 for o in outs)
+        e2e = {"value": world * w.K * w.sweeps / tj, "unit": UNIT,
+               "h2d_bytes_per_step": h2d / w.sweeps, "d2h_bytes_per_step": d2h / w.sweeps,
+               "job": f"create from pinned host buffers + {w.sweeps} sweeps + losses and factors to host, "
+                      f"median of {args.e2e_reps}", "job_seconds": tj}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = run_cpu_baseline(args.seconds)
+
+    if rank == 0:
+        out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": 1e3 * dev_s_max / args.steps,
+               "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+               "dtype": "f64" if args.precision == "fp64" else args.precision,
+               "data": "synthetic",
+               "config": {"workload": WORKLOAD, "precision": args.precision, "blocks": w.K, "C": w.C,
+                          "dims": list(w.dims), "sweeps_per_step": 1, "l2": "flushed between steps (256 MiB write)",
+                          "splits": splits, "graph": True, "parallelism": f"replicas x{world} (submodels independent)"},
+               "mttkrp_tflops": achieved,
+               "wall_ms_per_step": 1e3 * wall_max / args.steps,
+               "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+               "gpu_launches": kps * args.steps, "clocks": clocks,
+               "vs_plain_fp64": fp64,
+               "final_loss_median": float(np.nanmedian(losses_final))}
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.cpu_worker:
+        cpu_worker(args.seconds)
+        return
+    if args.impl == "reference":
+        reference_arm(args)
+        return
+    gpu_arm(args)
+
+
+if __name__ == "__main__":
+    main()

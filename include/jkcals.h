@@ -1,0 +1,218 @@
+/*
+ * jkcals.h -- C ABI of the GB300-native JK-CALS library (libjkcals.so).
+ *
+ * JK-CALS (Psarras, Karlsson, Bro, Bientinesi, "Accelerating jackknife
+ * resampling for the Canonical Polyadic Decomposition") fits every jackknife
+ * submodel of a CP model at once.  Each submodel g leaves out a set D_g of
+ * samples (indices of the sampled mode n_hat; leave-one-out: D_g = {g}).  Its
+ * factor matrices sit side by side in "multi-matrices" Ubar^(n) (I_n x C,
+ * C = sum_g R_g), and rows D_g of block g of Ubar^(n_hat) are kept at zero, so
+ * that one MTTKRP with the *full* tensor serves every resampled tensor
+ * (Sec. 4.1, Case I and Case II; Alg. 3).
+ *
+ * Notation used below: N modes (order of the tensor), dims I_0..I_{N-1}
+ * (0-based: mode n here is mode n+1 of the paper), K blocks (submodels),
+ * R_g components of block g, C = sum_g R_g, block g owns columns
+ * [off_g, off_g + R_g) with off_g = R_0 + ... + R_{g-1}.
+ *
+ * Conventions shared by every call:
+ *  - Memory.  Every pointer argument that carries data (tensor, factors,
+ *    outputs) may point to host memory or to device memory of the handle's
+ *    device; the library copies with unified addressing (cudaMemcpyDefault).
+ *    The caller owns those buffers.  The library owns its workspace, its own
+ *    copies of the tensor and factors, and its CUDA graphs.
+ *  - Layouts.  The tensor is dense C-order (last index fastest), FP64 or FP32.
+ *    Factor multi-matrices are row-major I_n x C, FP64.
+ *  - Streams.  Work is enqueued on the stream given at create (NULL = the
+ *    legacy default stream).  Calls that return values in host memory
+ *    synchronise that stream before returning.
+ *  - Errors.  Every call returns a jkcals_status and never throws across the
+ *    ABI.  jkcals_last_error() gives a thread-local message for the last
+ *    failing call of the calling thread.  A sticky CUDA error maps to
+ *    JKCALS_ERR_CUDA and leaves the handle in the STATE error (destroy only).
+ *  - Threads.  A handle may be used by one thread at a time.
+ */
+#ifndef JKCALS_H
+#define JKCALS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct jkcals_ctx* jkcals_t;
+
+typedef enum {
+  JKCALS_OK = 0,
+  JKCALS_ERR_ARG = 1,         /* invalid argument; nothing was enqueued          */
+  JKCALS_ERR_CUDA = 2,        /* a CUDA runtime/driver call failed               */
+  JKCALS_ERR_OOM = 3,         /* device allocation failed (or hit the cap)       */
+  JKCALS_ERR_NOT_SPD = 4,     /* some submodel met a non-SPD H (see block status) */
+  JKCALS_ERR_TIMEOUT = 5,     /* a bounded device wait gave up                   */
+  JKCALS_ERR_STATE = 6,       /* handle unusable after an earlier fatal error    */
+  JKCALS_ERR_UNSUPPORTED = 7  /* valid but outside this build's limits           */
+} jkcals_status;
+
+/* Arithmetic of the concurrent MTTKRP (Alg. 3 MTTKRP line).  The Gram,
+ * Cholesky, solve, normalisation and error kernels are FP64 in every form.  */
+typedef enum {
+  JKCALS_FP64 = 0,        /* FP64 products and sums (CUDA cores)                       */
+  JKCALS_TF32 = 1,        /* tcgen05 kind::tf32, FP32 accumulation in TMEM             */
+  JKCALS_3XTF32 = 2,      /* hi*hi + hi*lo + lo*hi TF32 products, FP32 accumulation    */
+  JKCALS_BF16 = 3,        /* tcgen05 kind::f16 with BF16 operands, FP32 accumulation   */
+  JKCALS_SPLIT_BF16 = 4   /* BF16 hi/mid/lo split, 6 cross products, FP32 accumulation */
+} jkcals_prec;
+
+typedef enum { JKCALS_DTYPE_F32 = 0, JKCALS_DTYPE_F64 = 1 } jkcals_dtype;
+
+/* Per-block status bits (jkcals_get_block_status). */
+#define JKCALS_BLOCK_NOT_SPD 1    /* Cholesky failed; block frozen since          */
+#define JKCALS_BLOCK_CONVERGED 2  /* tolerance test met; block frozen since       */
+
+typedef struct {
+  int precision;        /* jkcals_prec, default JKCALS_FP64                               */
+  int normalise;        /* 1 (default): after updating mode n < N-1, scale each column of
+                           every block to unit 2-norm (a zero column is left as is)       */
+  int use_graph;        /* 1 (default): replay sweeps from a captured CUDA graph          */
+  int splits;           /* 0 (default) = automatic split-K factor of the MTTKRP, else fixed */
+  int64_t max_device_bytes; /* 0 (default) = no cap; > 0: allocations beyond this many bytes
+                               fail with JKCALS_ERR_OOM (lets callers bound device memory) */
+  int kernel_timing;    /* 1: record CUDA events around every MTTKRP launch of a sweep
+                           (read with jkcals_kernel_times); 0 (default): off            */
+  int reserved[7];
+} jkcals_options;
+
+/* Fill *opt with the defaults above. */
+void jkcals_default_options(jkcals_options* opt);
+
+/*
+ * jkcals_create -- Alg. 3 initialisation (the loop that builds one factor
+ * multi-matrix per mode): copy the tensor into per-mode unfoldings T_(n)
+ * (Sec. 3.1, columns ordered by Eq. kolda_mapping), compute ||T_{-g}||^2 for
+ * the error line of Alg. 3, copy the initial multi-matrices, zero rows D_g of
+ * block g in mode sampled_mode (Alg. 3, red branch of the initialisation) and
+ * compute the per-block Grams.
+ *
+ *  out           receives the handle (NULL on failure)
+ *  N, dims       order (1 <= N <= 8 ... see limits) and the N dims, each >= 1
+ *  T, T_dtype    dense C-order tensor, host or device, JKCALS_DTYPE_F32/F64;
+ *                copied during the call, may be freed on return
+ *  sampled_mode  n_hat, 0 <= sampled_mode < N
+ *  K, ranks      number of blocks (>= 1) and R_g for each (1 <= R_g <= 32)
+ *  left_out_ptr  K+1 offsets into left_out_idx (CSR, left_out_ptr[0] = 0)
+ *  left_out_idx  the indices D_g, each in [0, dims[sampled_mode]); an empty
+ *                set makes block g the model of the full tensor
+ *  init          N pointers, init[n] is the I_n x C row-major FP64 initial
+ *                multi-matrix (host or device), copied during the call
+ *  opt           options or NULL for the defaults
+ *  stream        cudaStream_t as void*, NULL = legacy default stream
+ *
+ * Limits: N <= 8, R_g <= 32, prod(dims) < 2^40.
+ * Errors: ARG on any invalid value, OOM, CUDA, UNSUPPORTED (limits).
+ */
+jkcals_status jkcals_create(jkcals_t* out, int N, const int64_t* dims, const void* T, int T_dtype,
+                            int sampled_mode, int K, const int32_t* ranks,
+                            const int64_t* left_out_ptr, const int64_t* left_out_idx,
+                            const double* const* init, const jkcals_options* opt, void* stream);
+
+/* Release every resource of the handle (NULL is ignored).  Synchronises the stream. */
+void jkcals_destroy(jkcals_t h);
+
+/*
+ * jkcals_mttkrp -- the concurrent MTTKRP of Alg. 3 (MTTKRP line):
+ *   Mbar_n = T_(n) (Ubar^(N-1) (.) ... (.) Ubar^(n+1) (.) Ubar^(n-1) (.) ... (.) Ubar^(0))
+ * for the handle's current multi-matrices, in the handle's precision.  Block
+ * g's columns equal submodel g's own MTTKRP on its sliced tensor (Sec. 4.1);
+ * for mode == sampled_mode rows D_g of block g are the full-tensor values that
+ * Case I discards.
+ *  M_out   I_mode x C row-major FP64, host or device.
+ * Errors: ARG (mode out of range, NULL), CUDA, STATE.
+ */
+jkcals_status jkcals_mttkrp(jkcals_t h, int mode, double* M_out);
+
+/*
+ * jkcals_als_sweep -- nsweeps iterations of the repeat loop of Alg. 3: for
+ * every mode n, the concurrent MTTKRP, then per block the Hadamard of Grams,
+ * the Cholesky solve of the update line, zeroing of rows D_g in the sampled
+ * mode, column normalisation (modes n < N-1, if enabled) and the Gram
+ * refresh; after the last mode, the per-block error of the Alg. 3 error line
+ * (read with '+' before the model-norm term):
+ *   e_g = ||T_{-g}||^2 + sum(H_{N-1,g} * G_{N-1,g}) - 2 sum(Ubar_{N-1|g} * Mbar_{N-1|g}).
+ * Blocks frozen (NOT_SPD or CONVERGED) keep their factors; their losses are NaN.
+ *  losses  NULL or nsweeps x K FP64 (host or device): e_g after each sweep.
+ * Returns NOT_SPD if any block has the NOT_SPD bit after the call (the other
+ * blocks were still advanced); OK otherwise.
+ */
+jkcals_status jkcals_als_sweep(jkcals_t h, int nsweeps, double* losses);
+
+/*
+ * jkcals_als_sweep_async -- the sweeps of jkcals_als_sweep, only enqueued on the
+ * handle's stream: no host synchronisation and no status check (read the block
+ * status with jkcals_get_block_status).
+ *  losses_dev  NULL or nsweeps x K FP64 in device memory.
+ */
+jkcals_status jkcals_als_sweep_async(jkcals_t h, int nsweeps, double* losses_dev);
+
+/*
+ * jkcals_kernel_times -- device time of each mode's concurrent MTTKRP launch in
+ * the last completed sweep (requires opt.kernel_timing = 1; synchronises).
+ *  ms  N doubles (host), milliseconds per mode.
+ */
+jkcals_status jkcals_kernel_times(jkcals_t h, double* ms);
+
+/*
+ * jkcals_sweep_info -- how one sweep is executed on the device.
+ *  kernels_per_sweep  receives the number of kernel launches of one sweep
+ *  splits             NULL or N ints (host): the split-K factor of each mode's MTTKRP
+ */
+jkcals_status jkcals_sweep_info(jkcals_t h, int* kernels_per_sweep, int* splits);
+
+/*
+ * jkcals_run -- sweeps until every block is frozen or max_sweeps is reached.
+ * With tol > 0 a block converges when |e_prev - e| / ||T_{-g}||^2 < tol
+ * (stopping rule of Alg. 1/Alg. 3) and is frozen from then on.
+ *  sweeps_done  NULL or receives the number of sweeps run (host)
+ *  final_loss   NULL or K FP64 (host or device): the last finite e_g per block
+ */
+jkcals_status jkcals_run(jkcals_t h, int max_sweeps, double tol, int* sweeps_done,
+                         double* final_loss);
+
+/* Copy the current multi-matrices out: U[n] is I_n x C row-major FP64 (host or device). */
+jkcals_status jkcals_get_factors(jkcals_t h, double* const* U);
+
+/* Replace the multi-matrices (checkpoint resume); rows D_g of the sampled mode are
+ * zeroed again and the Grams recomputed.  Clears the CONVERGED bits and the stored
+ * previous losses.  U[n]: I_n x C row-major FP64 (host or device). */
+jkcals_status jkcals_set_factors(jkcals_t h, const double* const* U);
+
+/* Per-block status bits (JKCALS_BLOCK_*), K int32 (host). */
+jkcals_status jkcals_get_block_status(jkcals_t h, int32_t* status);
+
+/*
+ * jkcals_grad -- gradient of the summed reconstruction loss over all blocks,
+ *   f = sum_g ||T_{-g} - [[Ubar^(0)_{|g}, ..., Ubar^(N-1)_{|g}]]||^2,
+ * at the multi-matrices U (NULL = the handle's current ones; U is then taken
+ * with rows D_g of the sampled mode zeroed).  The gradient of block g with
+ * respect to Ubar^(n)_{|g} is 2 (Ubar^(n)_{|g} H^(n)_g - Mbar_{n|g}) (the
+ * normal equations of the update line of Alg. 1 written as a gradient), with
+ * Mbar_n the concurrent MTTKRP; rows D_g of the sampled mode get 0.
+ *  G     N pointers, G[n] is I_n x C row-major FP64 (host or device), or NULL
+ *  loss  NULL or one FP64 in host memory: f
+ */
+jkcals_status jkcals_grad(jkcals_t h, const double* const* U, double* const* G, double* loss);
+
+/* Block until the handle's stream is idle. */
+jkcals_status jkcals_sync(jkcals_t h);
+
+/* Thread-local message of the last failing call ("" if none). */
+const char* jkcals_last_error(void);
+
+/* Library version string. */
+const char* jkcals_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* JKCALS_H */

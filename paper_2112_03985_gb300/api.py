@@ -1,0 +1,219 @@
+"""Python binding of the C ABI: the same calls as include/jkcals.h, taking NumPy
+arrays (host) or torch tensors (host or CUDA).  It only marshals arguments;
+every step of the computation runs in libjkcals.so.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+from typing import List, Optional, Sequence
+
+import numpy as np
+
+from . import _lib as L
+
+__all__ = ["JKCALS", "JKError", "from_workload", "left_out_csr", "multi_init"]
+
+JKError = L.JKError
+
+
+def _ptr(x) -> int:
+    """Device or host address of a contiguous NumPy array / torch tensor."""
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return x.ctypes.data
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return x.data_ptr()
+    raise TypeError(f"unsupported buffer type {type(x)}")
+
+
+def _dtype_code(x) -> int:
+    name = str(x.dtype)
+    if name.endswith("float64"):
+        return L.DTYPE_F64
+    if name.endswith("float32"):
+        return L.DTYPE_F32
+    raise TypeError(f"tensor dtype must be float32 or float64, got {x.dtype}")
+
+
+def left_out_csr(left_out: Sequence[Sequence[int]]):
+    ptr = np.zeros(len(left_out) + 1, dtype=np.int64)
+    for g, D in enumerate(left_out):
+        ptr[g + 1] = ptr[g] + len(D)
+    idx = np.concatenate([np.asarray(D, dtype=np.int64) for D in left_out]) if ptr[-1] else np.zeros(1, np.int64)
+    return ptr, np.ascontiguousarray(idx)
+
+
+def multi_init(init_blocks: Sequence[Sequence[np.ndarray]]) -> List[np.ndarray]:
+    """Concatenate per-block initial factors side by side (Alg. 3 initialisation)."""
+    N = len(init_blocks[0])
+    return [np.ascontiguousarray(np.concatenate([np.asarray(b[n], dtype=np.float64) for b in init_blocks], axis=1))
+            for n in range(N)]
+
+
+def _torch():
+    import torch
+    return torch
+
+
+class JKCALS:
+    """Handle of one jackknife problem (jkcals_create ... jkcals_destroy)."""
+
+    def __init__(self, T, n_hat: int, ranks: Sequence[int], left_out: Sequence[Sequence[int]],
+                 init: Sequence, *, precision: str = "fp64", normalise: bool = True,
+                 use_graph: bool = True, splits: int = 0, max_device_bytes: int = 0,
+                 kernel_timing: bool = False, stream=None):
+        lib = L.load()
+        self._lib = lib
+        self._h = ct.c_void_p()
+        self.dims = tuple(int(d) for d in T.shape)
+        self.N = len(self.dims)
+        self.K = len(ranks)
+        self.ranks = [int(r) for r in ranks]
+        self.C = int(sum(self.ranks))
+        self.n_hat = int(n_hat)
+        self.precision = precision
+        opt = L.Options()
+        lib.jkcals_default_options(ct.byref(opt))
+        opt.precision = L.PREC[precision]
+        opt.normalise = int(bool(normalise))
+        opt.use_graph = int(bool(use_graph))
+        opt.splits = int(splits)
+        opt.max_device_bytes = int(max_device_bytes)
+        opt.kernel_timing = int(bool(kernel_timing))
+        dims = (ct.c_int64 * self.N)(*self.dims)
+        rk = (ct.c_int32 * self.K)(*self.ranks)
+        ptr, idx = left_out_csr(left_out)
+        self._keep = [T, ptr, idx, init]
+        init_ptrs = (ct.c_void_p * self.N)(*[_ptr(u) for u in init])
+        for n, u in enumerate(init):
+            if tuple(u.shape) != (self.dims[n], self.C):
+                raise ValueError(f"init[{n}] must be {self.dims[n]} x {self.C}")
+            if "float64" not in str(u.dtype):
+                raise TypeError("init factors must be float64")
+        if stream is None and hasattr(T, "is_cuda") and T.is_cuda:
+            stream = _torch().cuda.current_stream().cuda_stream
+        st = L.check(lib.jkcals_create(ct.byref(self._h), self.N, dims, ct.c_void_p(_ptr(T)), _dtype_code(T),
+                                       self.n_hat, self.K, rk,
+                                       ptr.ctypes.data_as(L.I64P), idx.ctypes.data_as(L.I64P),
+                                       init_ptrs, ct.byref(opt), ct.c_void_p(stream) if stream else None),
+                     "jkcals_create")
+        del st
+        self._keep = None
+
+    # -- lifecycle -------------------------------------------------------------
+    def close(self):
+        if self._h:
+            self._lib.jkcals_destroy(self._h)
+            self._h = ct.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # -- calls -------------------------------------------------------------------
+    def _out(self, shape, device):
+        if device is None or device == "cpu":
+            return np.empty(shape, dtype=np.float64)
+        torch = _torch()
+        return torch.empty(shape, dtype=torch.float64, device=device)
+
+    def mttkrp(self, mode: int, out=None, device=None):
+        """Concurrent MTTKRP of Alg. 3 for the current factors: I_mode x C FP64."""
+        if out is None:
+            out = self._out((self.dims[mode], self.C), device)
+        L.check(self._lib.jkcals_mttkrp(self._h, int(mode), ct.c_void_p(_ptr(out))), "jkcals_mttkrp")
+        return out
+
+    def als_sweep(self, nsweeps: int, losses=True, device=None, raise_not_spd: bool = False):
+        """nsweeps JK-CALS sweeps; returns the nsweeps x K losses (or None)."""
+        out = None
+        if losses is True:
+            out = self._out((nsweeps, self.K), device)
+        elif losses is not None and losses is not False:
+            out = losses
+        st = self._lib.jkcals_als_sweep(self._h, int(nsweeps), ct.c_void_p(_ptr(out)) if out is not None else None)
+        if st != L.ERR_NOT_SPD or raise_not_spd:
+            L.check(st, "jkcals_als_sweep")
+        return out
+
+    def als_sweep_async(self, nsweeps: int, losses_dev=None):
+        """Enqueue nsweeps sweeps without synchronising (losses_dev: CUDA tensor or None)."""
+        L.check(self._lib.jkcals_als_sweep_async(self._h, int(nsweeps),
+                                                 ct.c_void_p(_ptr(losses_dev)) if losses_dev is not None else None),
+                "jkcals_als_sweep_async")
+        return losses_dev
+
+    def kernel_times(self):
+        """Per-mode MTTKRP device time (ms) of the last completed sweep (kernel_timing=True)."""
+        ms = (ct.c_double * self.N)()
+        L.check(self._lib.jkcals_kernel_times(self._h, ms), "jkcals_kernel_times")
+        return list(ms)
+
+    def sweep_info(self):
+        k = ct.c_int(0)
+        sp = (ct.c_int * self.N)()
+        L.check(self._lib.jkcals_sweep_info(self._h, ct.byref(k), sp), "jkcals_sweep_info")
+        return k.value, list(sp)
+
+    def run(self, max_sweeps: int, tol: float = 0.0):
+        done = ct.c_int(0)
+        fl = np.empty(self.K, dtype=np.float64)
+        st = self._lib.jkcals_run(self._h, int(max_sweeps), float(tol), ct.byref(done), ct.c_void_p(fl.ctypes.data))
+        if st != L.ERR_NOT_SPD:
+            L.check(st, "jkcals_run")
+        return done.value, fl
+
+    def get_factors_into(self, outs):
+        return self.get_factors(outs=outs)
+
+    def get_factors(self, device=None, outs=None):
+        if outs is None:
+            outs = [self._out((I, self.C), device) for I in self.dims]
+        arr = (ct.c_void_p * self.N)(*[_ptr(o) for o in outs])
+        L.check(self._lib.jkcals_get_factors(self._h, arr), "jkcals_get_factors")
+        return outs
+
+    def set_factors(self, U):
+        arr = (ct.c_void_p * self.N)(*[_ptr(u) for u in U])
+        L.check(self._lib.jkcals_set_factors(self._h, arr), "jkcals_set_factors")
+
+    def block_status(self):
+        st = np.zeros(self.K, dtype=np.int32)
+        L.check(self._lib.jkcals_get_block_status(self._h, st.ctypes.data_as(L.I32P)), "jkcals_get_block_status")
+        return st
+
+    def grad(self, U=None, G=None, device=None, want_grad: bool = True):
+        """Summed jackknife loss and its gradient w.r.t. the multi-matrices."""
+        Uarr = (ct.c_void_p * self.N)(*[_ptr(u) for u in U]) if U is not None else None
+        if want_grad and G is None:
+            G = [self._out((I, self.C), device) for I in self.dims]
+        Garr = (ct.c_void_p * self.N)(*[_ptr(g) for g in G]) if G is not None else None
+        loss = ct.c_double(0.0)
+        L.check(self._lib.jkcals_grad(self._h, Uarr, Garr, ct.byref(loss)), "jkcals_grad")
+        return loss.value, G
+
+    def sync(self):
+        L.check(self._lib.jkcals_sync(self._h), "jkcals_sync")
+
+
+def from_workload(w, precision: str = "fp64", device: Optional[str] = None, **kw) -> JKCALS:
+    """Handle for a ``workloads.Workload`` (tensor in its dtype, init side by side)."""
+    T = w.T.astype(np.float32) if w.dtype == "f32" else w.T
+    T = np.ascontiguousarray(T)
+    init = multi_init(w.init)
+    if device is not None and device != "cpu":
+        torch = _torch()
+        T = torch.from_numpy(T).to(device)
+        init = [torch.from_numpy(u).to(device) for u in init]
+    return JKCALS(T, w.n_hat, w.ranks, w.left_out, init, precision=precision, **kw)

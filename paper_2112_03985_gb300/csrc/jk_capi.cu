@@ -1,0 +1,704 @@
+// C ABI of libjkcals.so: handle lifecycle, planning, and the host-side
+// orchestration of Alg. 3 (one concurrent MTTKRP + one fused per-block update
+// per mode, the error after the last mode), replayed from a CUDA graph.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "jk_common.cuh"
+
+namespace jk {
+thread_local std::string g_last_error;
+void set_error(const std::string& msg) { g_last_error = msg; }
+}  // namespace jk
+
+using namespace jk;
+
+namespace {
+
+constexpr int kMttkrpBK = 16;   // k-step of the FP64 MTTKRP kernel
+constexpr int kMttkrpBM = 64;
+constexpr int kMttkrpBN = 64;
+
+jkcals_status fail(jkcals_status s, const std::string& msg) {
+  set_error(msg);
+  return s;
+}
+
+jkcals_status fail_cuda(jkcals_ctx* h, cudaError_t e, const char* what) {
+  std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();
+    return fail(JKCALS_ERR_OOM, m);
+  }
+  if (h != nullptr) {
+    // Sticky errors poison the context; a later call returns STATE.
+    cudaError_t sticky = cudaDeviceSynchronize();
+    if (sticky != cudaSuccess) h->broken = true;
+  }
+  return fail(JKCALS_ERR_CUDA, m);
+}
+
+#define JK_CUDA(h, call)                                   \
+  do {                                                     \
+    cudaError_t e_ = (call);                               \
+    if (e_ != cudaSuccess) return fail_cuda((h), e_, #call); \
+  } while (0)
+
+#define JK_TRY(call)                         \
+  do {                                       \
+    jkcals_status s_ = (call);               \
+    if (s_ != JKCALS_OK) return s_;          \
+  } while (0)
+
+jkcals_status dalloc(jkcals_ctx* h, void** p, size_t bytes) {
+  *p = nullptr;
+  if (bytes == 0) bytes = 16;
+  if (h->opt.max_device_bytes > 0 && h->bytes_allocated + (int64_t)bytes > h->opt.max_device_bytes)
+    return fail(JKCALS_ERR_OOM, "device memory cap (max_device_bytes) reached");
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    return fail_cuda(nullptr, e, "cudaMalloc");
+  }
+  h->allocations.push_back(*p);
+  h->bytes_allocated += (int64_t)bytes;
+  return JKCALS_OK;
+}
+
+template <typename T>
+jkcals_status dalloc_t(jkcals_ctx* h, T** p, size_t count) {
+  void* v = nullptr;
+  jkcals_status s = dalloc(h, &v, count * sizeof(T));
+  *p = static_cast<T*>(v);
+  return s;
+}
+
+void dfree(jkcals_ctx* h, void* p) {
+  if (p == nullptr) return;
+  auto it = std::find(h->allocations.begin(), h->allocations.end(), p);
+  if (it != h->allocations.end()) h->allocations.erase(it);
+  cudaFree(p);
+}
+
+bool is_host_pointer(const void* p) {
+  cudaPointerAttributes attr{};
+  cudaError_t e = cudaPointerGetAttributes(&attr, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return true;
+  }
+  return attr.type == cudaMemoryTypeHost || attr.type == cudaMemoryTypeUnregistered;
+}
+
+BlockMeta block_meta(const jkcals_ctx* h) {
+  BlockMeta bm;
+  bm.R = h->d_R;
+  bm.off = h->d_off;
+  bm.gram_off = h->d_gram_off;
+  bm.lo_ptr = h->d_lo_ptr;
+  bm.lo_idx = h->d_lo_idx;
+  return bm;
+}
+
+KrpOperands krp_operands(const jkcals_ctx* h, int n, double* const* U) {
+  KrpOperands kr{};
+  int o = 0;
+  for (int k = 0; k < h->N; ++k) {
+    if (k == n) continue;
+    kr.U[o] = U[k];
+    kr.dims[o] = (int)h->dims[k];
+    ++o;
+  }
+  kr.nother = o;
+  return kr;
+}
+
+void make_plan(jkcals_ctx* h) {
+  const int target = 4 * h->num_sms;
+  for (int n = 0; n < h->N; ++n) {
+    ModePlan& p = h->plan[n];
+    const int64_t I = h->dims[n], J = h->J[n];
+    const int64_t tiles = ((I + kMttkrpBM - 1) / kMttkrpBM) * ((h->C + kMttkrpBN - 1) / kMttkrpBN);
+    const int64_t ksteps = (J + kMttkrpBK - 1) / kMttkrpBK;
+    int64_t S = h->opt.splits > 0 ? h->opt.splits : (target + tiles - 1) / tiles;
+    if (h->opt.splits <= 0) S = std::min<int64_t>(S, std::max<int64_t>(1, ksteps / 4));
+    S = std::max<int64_t>(1, std::min<int64_t>(S, ksteps));
+    int64_t kchunk = ((ksteps + S - 1) / S) * kMttkrpBK;
+    S = (J + kchunk - 1) / kchunk;
+    p.splits = (int)S;
+    p.kchunk = kchunk;
+    // update: about two CTAs per SM, at most 128 rows per chunk
+    int64_t RC = std::max<int64_t>(1, (2 * h->num_sms + h->K - 1) / h->K);
+    RC = std::min<int64_t>(RC, std::max<int64_t>(1, (I + 31) / 32));
+    int64_t rpc = (I + RC - 1) / RC;
+    if (rpc > 128) {
+      RC = (I + 127) / 128;
+      rpc = (I + RC - 1) / RC;
+    }
+    RC = (I + rpc - 1) / rpc;
+    p.upd.rows_per_chunk = (int)rpc;
+    p.upd.RC = (int)RC;
+  }
+}
+
+jkcals_status ensure_loss_cap(jkcals_ctx* h, int need) {
+  if (need <= h->loss_cap) return JKCALS_OK;
+  if (h->loss_hist) dfree(h, h->loss_hist);
+  h->loss_hist = nullptr;
+  h->loss_cap = 0;
+  int cap = std::max(need, 64);
+  JK_TRY(dalloc_t(h, &h->loss_hist, (size_t)cap * h->K));
+  h->loss_cap = cap;
+  if (h->sweep_exec) {
+    cudaGraphExecDestroy(h->sweep_exec);
+    h->sweep_exec = nullptr;
+  }
+  h->graph_valid = false;
+  return JKCALS_OK;
+}
+
+UpdateArgs update_args(jkcals_ctx* h, int n, const void* part, int part_is_f32, int S) {
+  UpdateArgs a{};
+  a.N = h->N;
+  a.n = n;
+  a.n_hat = h->n_hat;
+  a.K = h->K;
+  a.C = h->C;
+  a.I = h->dims[n];
+  a.bm = block_meta(h);
+  a.U = h->U[n];
+  for (int k = 0; k < h->N; ++k) a.gram[k] = h->gram[k];
+  a.gram_n = h->gram[n];
+  a.part = part;
+  a.part_is_f32 = part_is_f32;
+  a.S = S;
+  a.rows_per_chunk = h->plan[n].upd.rows_per_chunk;
+  a.RC = h->plan[n].upd.RC;
+  a.gpart = h->gpart;
+  a.fpart = h->fpart;
+  a.status = h->d_status;
+  a.normalise = h->opt.normalise;
+  a.normT2 = h->d_normT2;
+  a.loss_prev = h->d_loss_prev;
+  a.loss_last = h->d_loss_last;
+  a.tol = h->d_tol;
+  a.loss_hist = h->loss_hist;
+  a.loss_cap = h->loss_cap;
+  a.sweep_idx = h->d_sweep_idx;
+  return a;
+}
+
+// Enqueue the concurrent MTTKRP of mode n for factor set U into h->part.
+jkcals_status enqueue_mttkrp(jkcals_ctx* h, int n, double* const* U) {
+  const ModePlan& p = h->plan[n];
+  KrpOperands kr = krp_operands(h, n, U);
+  JK_CUDA(h, launch_mttkrp_f64(h->Tn64[n], h->dims[n], h->J[n], h->C, kr, p.splits, p.kchunk,
+                               static_cast<double*>(h->part), h->stream));
+  return JKCALS_OK;
+}
+
+jkcals_status enqueue_sweep(jkcals_ctx* h) {
+  int kernels = 0;
+  for (int n = 0; n < h->N; ++n) {
+    if (h->opt.kernel_timing) JK_CUDA(h, cudaEventRecord(h->ev_start[n], h->stream));
+    JK_TRY(enqueue_mttkrp(h, n, h->U));
+    if (h->opt.kernel_timing) JK_CUDA(h, cudaEventRecord(h->ev_stop[n], h->stream));
+    UpdateArgs a = update_args(h, n, h->part, 0, h->plan[n].splits);
+    JK_CUDA(h, launch_update(a, h->stream));
+    kernels += 3;
+  }
+  JK_CUDA(h, launch_advance_sweep(h->d_sweep_idx, h->stream));
+  h->kernels_per_sweep = kernels + 1;
+  return JKCALS_OK;
+}
+
+jkcals_status build_graph(jkcals_ctx* h) {
+  if (h->graph_valid) return JKCALS_OK;
+  if (h->sweep_exec) {
+    cudaGraphExecDestroy(h->sweep_exec);
+    h->sweep_exec = nullptr;
+  }
+  JK_CUDA(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+  jkcals_status s = enqueue_sweep(h);
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamEndCapture(h->stream, &graph);
+  if (s != JKCALS_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return s;
+  }
+  if (e != cudaSuccess) return fail_cuda(h, e, "cudaStreamEndCapture");
+  e = cudaGraphInstantiate(&h->sweep_exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return fail_cuda(h, e, "cudaGraphInstantiate");
+  h->graph_valid = true;
+  return JKCALS_OK;
+}
+
+jkcals_status run_sweeps(jkcals_ctx* h, int nsweeps) {
+  if (h->opt.use_graph) {
+    JK_TRY(build_graph(h));
+    for (int s = 0; s < nsweeps; ++s) JK_CUDA(h, cudaGraphLaunch(h->sweep_exec, h->stream));
+  } else {
+    for (int s = 0; s < nsweeps; ++s) JK_TRY(enqueue_sweep(h));
+  }
+  return JKCALS_OK;
+}
+
+jkcals_status refresh_factor_state(jkcals_ctx* h) {
+  BlockMeta bm = block_meta(h);
+  JK_CUDA(h, launch_zero_left_out(h->U[h->n_hat], h->C, h->K, bm, h->stream));
+  for (int n = 0; n < h->N; ++n)
+    JK_CUDA(h, launch_grams(h->U[n], h->dims[n], h->C, h->K, bm, h->gram[n], h->stream));
+  JK_CUDA(h, cudaMemsetAsync(h->d_status, 0, sizeof(int32_t) * h->K, h->stream));
+  JK_CUDA(h, cudaMemsetAsync(h->d_loss_prev, 0xff, sizeof(double) * h->K, h->stream));
+  JK_CUDA(h, cudaMemsetAsync(h->d_loss_last, 0xff, sizeof(double) * h->K, h->stream));
+  return JKCALS_OK;
+}
+
+jkcals_status copy_out(jkcals_ctx* h, void* dst, const void* src, size_t bytes) {
+  JK_CUDA(h, cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, h->stream));
+  if (is_host_pointer(dst)) JK_CUDA(h, cudaStreamSynchronize(h->stream));
+  return JKCALS_OK;
+}
+
+jkcals_status check_handle(jkcals_t h) {
+  if (h == nullptr) return fail(JKCALS_ERR_ARG, "NULL handle");
+  if (h->broken) return fail(JKCALS_ERR_STATE, "handle unusable after an earlier CUDA error");
+  JK_CUDA(h, cudaSetDevice(h->device));
+  return JKCALS_OK;
+}
+
+void destroy_impl(jkcals_ctx* h) {
+  if (h == nullptr) return;
+  int cur = 0;
+  cudaGetDevice(&cur);
+  cudaSetDevice(h->device);
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  if (h->sweep_exec) cudaGraphExecDestroy(h->sweep_exec);
+  for (int n = 0; n < kMaxModes; ++n) {
+    if (h->ev_start[n]) cudaEventDestroy(h->ev_start[n]);
+    if (h->ev_stop[n]) cudaEventDestroy(h->ev_stop[n]);
+  }
+  for (void* p : h->allocations) cudaFree(p);
+  h->allocations.clear();
+  if (h->stream && h->owns_stream) cudaStreamDestroy(h->stream);
+  cudaSetDevice(cur);
+  delete h;
+}
+
+}  // namespace
+
+namespace {
+
+jkcals_status create_impl(jkcals_ctx* h, const void* T, int T_dtype, const int32_t* ranks,
+                          const int64_t* left_out_ptr, const int64_t* left_out_idx,
+                          const double* const* init) {
+  const int N = h->N, K = h->K;
+  int64_t total = 1;
+  for (int k = 0; k < N; ++k) total *= h->dims[k];
+  for (int k = 0; k < N; ++k) h->J[k] = total / h->dims[k];
+
+  // block metadata
+  h->R.assign(ranks, ranks + K);
+  h->off.resize(K);
+  h->gram_off.resize(K);
+  int c = 0, go = 0;
+  for (int g = 0; g < K; ++g) {
+    h->off[g] = c;
+    h->gram_off[g] = go;
+    c += h->R[g];
+    go += h->R[g] * h->R[g];
+    h->Rmax = std::max(h->Rmax, h->R[g]);
+  }
+  h->C = c;
+  h->gram_total = go;
+  h->lo_ptr.assign(left_out_ptr, left_out_ptr + K + 1);
+  h->lo_idx.assign(left_out_idx, left_out_idx + left_out_ptr[K]);
+  for (int g = 0; g < K; ++g) std::sort(h->lo_idx.begin() + h->lo_ptr[g], h->lo_idx.begin() + h->lo_ptr[g + 1]);
+
+  JK_TRY(dalloc_t(h, &h->d_R, K));
+  JK_TRY(dalloc_t(h, &h->d_off, K));
+  JK_TRY(dalloc_t(h, &h->d_gram_off, K));
+  JK_TRY(dalloc_t(h, &h->d_lo_ptr, K + 1));
+  JK_TRY(dalloc_t(h, &h->d_lo_idx, std::max<size_t>(1, h->lo_idx.size())));
+  JK_TRY(dalloc_t(h, &h->d_status, K));
+  JK_TRY(dalloc_t(h, &h->d_normT2, K));
+  JK_TRY(dalloc_t(h, &h->d_loss_prev, K));
+  JK_TRY(dalloc_t(h, &h->d_loss_last, K));
+  JK_TRY(dalloc_t(h, &h->d_tol, 1));
+  JK_TRY(dalloc_t(h, &h->d_sweep_idx, 1));
+  cudaStream_t st = h->stream;
+  JK_CUDA(h, cudaMemcpyAsync(h->d_R, h->R.data(), sizeof(int) * K, cudaMemcpyHostToDevice, st));
+  JK_CUDA(h, cudaMemcpyAsync(h->d_off, h->off.data(), sizeof(int) * K, cudaMemcpyHostToDevice, st));
+  JK_CUDA(h, cudaMemcpyAsync(h->d_gram_off, h->gram_off.data(), sizeof(int) * K, cudaMemcpyHostToDevice, st));
+  JK_CUDA(h, cudaMemcpyAsync(h->d_lo_ptr, h->lo_ptr.data(), sizeof(int64_t) * (K + 1), cudaMemcpyHostToDevice, st));
+  if (!h->lo_idx.empty())
+    JK_CUDA(h, cudaMemcpyAsync(h->d_lo_idx, h->lo_idx.data(), sizeof(int64_t) * h->lo_idx.size(),
+                               cudaMemcpyHostToDevice, st));
+  JK_CUDA(h, cudaMemsetAsync(h->d_tol, 0, sizeof(double), st));
+  JK_CUDA(h, cudaMemsetAsync(h->d_sweep_idx, 0, sizeof(int), st));
+  // host-side vectors above are pageable: make sure the copies finished
+  JK_CUDA(h, cudaStreamSynchronize(st));
+
+  // tensor -> per-mode unfoldings (FP64)
+  double* Tc = nullptr;
+  JK_TRY(dalloc_t(h, &Tc, total));
+  if (T_dtype == JKCALS_DTYPE_F64) {
+    JK_CUDA(h, cudaMemcpyAsync(Tc, T, sizeof(double) * total, cudaMemcpyDefault, st));
+  } else {
+    float* T32 = nullptr;
+    JK_TRY(dalloc_t(h, &T32, total));
+    JK_CUDA(h, cudaMemcpyAsync(T32, T, sizeof(float) * total, cudaMemcpyDefault, st));
+    JK_CUDA(h, launch_f32_to_f64(T32, Tc, total, st));
+    JK_CUDA(h, cudaStreamSynchronize(st));
+    dfree(h, T32);
+  }
+  for (int n = 0; n < N; ++n) {
+    JK_TRY(dalloc_t(h, &h->Tn64[n], total));
+    JK_CUDA(h, launch_unfold_f64(Tc, h->dims, N, n, h->Tn64[n], st));
+  }
+  double* slice = nullptr;
+  JK_TRY(dalloc_t(h, &slice, h->dims[h->n_hat]));
+  JK_CUDA(h, launch_row_sumsq(h->Tn64[h->n_hat], h->dims[h->n_hat], h->J[h->n_hat], slice, st));
+  JK_CUDA(h, launch_block_norms(slice, h->dims[h->n_hat], K, block_meta(h), h->d_normT2, st));
+  JK_CUDA(h, cudaStreamSynchronize(st));
+  dfree(h, slice);
+  dfree(h, Tc);
+
+  // factors and Grams
+  int64_t Imax = 0;
+  for (int n = 0; n < N; ++n) {
+    JK_TRY(dalloc_t(h, &h->U[n], (size_t)h->dims[n] * h->C));
+    JK_TRY(dalloc_t(h, &h->gram[n], (size_t)h->gram_total));
+    JK_CUDA(h, cudaMemcpyAsync(h->U[n], init[n], sizeof(double) * h->dims[n] * h->C, cudaMemcpyDefault, st));
+    Imax = std::max(Imax, h->dims[n]);
+  }
+
+  // plan + workspace
+  make_plan(h);
+  size_t part_elems = 0, chunks = 0;
+  for (int n = 0; n < N; ++n) {
+    part_elems = std::max(part_elems, (size_t)h->plan[n].splits * h->dims[n] * h->C);
+    chunks = std::max(chunks, (size_t)h->plan[n].upd.RC * K);
+  }
+  h->part_bytes = part_elems * sizeof(double);
+  JK_TRY(dalloc(h, &h->part, h->part_bytes));
+  JK_TRY(dalloc_t(h, &h->gpart, chunks * kMaxRank * kMaxRank));
+  JK_TRY(dalloc_t(h, &h->fpart, chunks));
+  h->upd_chunks = chunks;
+  JK_TRY(dalloc_t(h, &h->mbuf, (size_t)Imax * h->C));
+  JK_TRY(ensure_loss_cap(h, 64));
+  if (h->opt.kernel_timing) {
+    for (int n = 0; n < N; ++n) {
+      JK_CUDA(h, cudaEventCreate(&h->ev_start[n]));
+      JK_CUDA(h, cudaEventCreate(&h->ev_stop[n]));
+    }
+  }
+  h->kernels_per_sweep = 3 * N + 1;
+  JK_TRY(refresh_factor_state(h));
+  JK_CUDA(h, cudaStreamSynchronize(st));
+  return JKCALS_OK;
+}
+
+jkcals_status grad_impl(jkcals_ctx* h, const double* const* U, double* const* G, double* loss) {
+  const int N = h->N;
+  cudaStream_t st = h->stream;
+  if (!h->grad_ready) {
+    for (int n = 0; n < N; ++n) {
+      JK_TRY(dalloc_t(h, &h->gU[n], (size_t)h->dims[n] * h->C));
+      JK_TRY(dalloc_t(h, &h->ggram[n], (size_t)h->gram_total));
+      JK_TRY(dalloc_t(h, &h->gG[n], (size_t)h->dims[n] * h->C));
+    }
+    JK_TRY(dalloc_t(h, &h->geg, (size_t)h->K + 1));
+    h->grad_ready = true;
+  }
+  BlockMeta bm = block_meta(h);
+  for (int n = 0; n < N; ++n) {
+    const double* src = U ? U[n] : h->U[n];
+    JK_CUDA(h, cudaMemcpyAsync(h->gU[n], src, sizeof(double) * h->dims[n] * h->C, cudaMemcpyDefault, st));
+  }
+  JK_CUDA(h, launch_zero_left_out(h->gU[h->n_hat], h->C, h->K, bm, st));
+  for (int n = 0; n < N; ++n)
+    JK_CUDA(h, launch_grams(h->gU[n], h->dims[n], h->C, h->K, bm, h->ggram[n], st));
+  for (int n = 0; n < N; ++n) {
+    JK_TRY(enqueue_mttkrp(h, n, h->gU));
+    const int64_t cnt = h->dims[n] * (int64_t)h->C;
+    JK_CUDA(h, launch_reduce_partials_f64(static_cast<double*>(h->part), h->plan[n].splits, cnt, h->mbuf, st));
+    if (G != nullptr && G[n] != nullptr) {
+      JK_CUDA(h, launch_grad_epilogue(N, n, h->n_hat, h->dims[n], h->C, h->K, bm, h->gU[n], h->ggram,
+                                      h->mbuf, h->gG[n], st));
+      JK_CUDA(h, cudaMemcpyAsync(G[n], h->gG[n], sizeof(double) * cnt, cudaMemcpyDefault, st));
+    }
+    if (n == N - 1)
+      JK_CUDA(h, launch_grad_loss(N, h->dims[n], h->C, h->K, bm, h->gU[n], h->ggram, h->mbuf,
+                                  h->d_normT2, h->geg, st));
+  }
+  if (loss != nullptr) {
+    JK_CUDA(h, cudaMemcpyAsync(loss, h->geg + h->K, sizeof(double), cudaMemcpyDefault, st));
+  }
+  JK_CUDA(h, cudaStreamSynchronize(st));
+  return JKCALS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void jkcals_default_options(jkcals_options* opt) {
+  if (!opt) return;
+  memset(opt, 0, sizeof(*opt));
+  opt->precision = JKCALS_FP64;
+  opt->normalise = 1;
+  opt->use_graph = 1;
+  opt->splits = 0;
+  opt->max_device_bytes = 0;
+}
+
+const char* jkcals_last_error(void) { return jk::g_last_error.c_str(); }
+
+const char* jkcals_version(void) { return "jkcals 0.1 (sm_103a)"; }
+
+jkcals_status jkcals_create(jkcals_t* out, int N, const int64_t* dims, const void* T, int T_dtype,
+                            int sampled_mode, int K, const int32_t* ranks,
+                            const int64_t* left_out_ptr, const int64_t* left_out_idx,
+                            const double* const* init, const jkcals_options* opt, void* stream) {
+  set_error("");
+  if (out == nullptr) return fail(JKCALS_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (N < 2 || N > kMaxModes) return fail(N < 2 ? JKCALS_ERR_ARG : JKCALS_ERR_UNSUPPORTED, "N must be in [2, 8]");
+  if (dims == nullptr || T == nullptr || ranks == nullptr || left_out_ptr == nullptr || init == nullptr)
+    return fail(JKCALS_ERR_ARG, "NULL argument");
+  if (T_dtype != JKCALS_DTYPE_F32 && T_dtype != JKCALS_DTYPE_F64) return fail(JKCALS_ERR_ARG, "bad T_dtype");
+  double vol = 1.0;
+  for (int k = 0; k < N; ++k) {
+    if (dims[k] < 1) return fail(JKCALS_ERR_ARG, "dims must be >= 1");
+    vol *= (double)dims[k];
+  }
+  if (vol >= 1099511627776.0) return fail(JKCALS_ERR_UNSUPPORTED, "prod(dims) must be < 2^40");
+  // grid limits: row chunks of 128 on grid.y of the update kernels
+  for (int k = 0; k < N; ++k)
+    if (dims[k] > 65535LL * 128) return fail(JKCALS_ERR_UNSUPPORTED, "dims must be <= 8388480");
+  if (sampled_mode < 0 || sampled_mode >= N) return fail(JKCALS_ERR_ARG, "sampled_mode out of range");
+  if (K < 1) return fail(JKCALS_ERR_ARG, "K must be >= 1");
+  int64_t Csum = 0;
+  for (int g = 0; g < K; ++g) {
+    if (ranks[g] < 1) return fail(JKCALS_ERR_ARG, "ranks must be >= 1");
+    if (ranks[g] > kMaxRank) return fail(JKCALS_ERR_UNSUPPORTED, "ranks must be <= 32");
+    Csum += ranks[g];
+  }
+  // column tiles of 64 on grid.y of the MTTKRP kernel
+  if (Csum > 65535LL * 64) return fail(JKCALS_ERR_UNSUPPORTED, "sum of ranks must be <= 4194240");
+  if (left_out_ptr[0] != 0) return fail(JKCALS_ERR_ARG, "left_out_ptr[0] must be 0");
+  for (int g = 0; g < K; ++g)
+    if (left_out_ptr[g + 1] < left_out_ptr[g]) return fail(JKCALS_ERR_ARG, "left_out_ptr must be non-decreasing");
+  if (left_out_ptr[K] > 0 && left_out_idx == nullptr) return fail(JKCALS_ERR_ARG, "left_out_idx is NULL");
+  const int64_t Ihat = dims[sampled_mode];
+  for (int g = 0; g < K; ++g) {
+    std::vector<int64_t> d(left_out_idx + left_out_ptr[g], left_out_idx + left_out_ptr[g + 1]);
+    std::sort(d.begin(), d.end());
+    for (size_t q = 0; q < d.size(); ++q) {
+      if (d[q] < 0 || d[q] >= Ihat) return fail(JKCALS_ERR_ARG, "left-out index out of range");
+      if (q > 0 && d[q] == d[q - 1]) return fail(JKCALS_ERR_ARG, "duplicate left-out index");
+    }
+    if ((int64_t)d.size() >= Ihat) return fail(JKCALS_ERR_ARG, "a block leaves out every sample");
+  }
+  for (int k = 0; k < N; ++k)
+    if (init[k] == nullptr) return fail(JKCALS_ERR_ARG, "init[n] is NULL");
+  jkcals_options o;
+  jkcals_default_options(&o);
+  if (opt) o = *opt;
+  if (o.precision != JKCALS_FP64)
+    return fail(JKCALS_ERR_UNSUPPORTED, "precision form not built in this library version");
+  if (o.splits < 0) return fail(JKCALS_ERR_ARG, "splits must be >= 0");
+
+  jkcals_ctx* h = new jkcals_ctx();
+  h->N = N;
+  for (int k = 0; k < N; ++k) h->dims[k] = dims[k];
+  h->n_hat = sampled_mode;
+  h->K = K;
+  h->opt = o;
+  cudaError_t e = cudaGetDevice(&h->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
+  if (e != cudaSuccess) {
+    delete h;
+    return fail_cuda(nullptr, e, "cudaGetDevice");
+  }
+  if (stream != nullptr) {
+    h->stream = static_cast<cudaStream_t>(stream);
+  } else {
+    // The legacy default stream cannot be captured into a graph; use a
+    // blocking stream, which synchronises with it implicitly.
+    e = cudaStreamCreate(&h->stream);
+    if (e != cudaSuccess) {
+      delete h;
+      return fail_cuda(nullptr, e, "cudaStreamCreate");
+    }
+    h->owns_stream = true;
+  }
+  jkcals_status s = create_impl(h, T, T_dtype, ranks, left_out_ptr, left_out_idx, init);
+  if (s != JKCALS_OK) {
+    std::string msg = g_last_error;
+    destroy_impl(h);
+    set_error(msg);
+    return s;
+  }
+  *out = h;
+  return JKCALS_OK;
+}
+
+void jkcals_destroy(jkcals_t h) { destroy_impl(h); }
+
+jkcals_status jkcals_mttkrp(jkcals_t h, int mode, double* M_out) {
+  JK_TRY(check_handle(h));
+  if (mode < 0 || mode >= h->N) return fail(JKCALS_ERR_ARG, "mode out of range");
+  if (M_out == nullptr) return fail(JKCALS_ERR_ARG, "M_out is NULL");
+  JK_TRY(enqueue_mttkrp(h, mode, h->U));
+  const int64_t cnt = h->dims[mode] * (int64_t)h->C;
+  JK_CUDA(h, launch_reduce_partials_f64(static_cast<double*>(h->part), h->plan[mode].splits, cnt, h->mbuf,
+                                        h->stream));
+  return copy_out(h, M_out, h->mbuf, sizeof(double) * cnt);
+}
+
+static jkcals_status any_not_spd(jkcals_ctx* h) {
+  std::vector<int32_t> st(h->K);
+  JK_CUDA(h, cudaMemcpyAsync(st.data(), h->d_status, sizeof(int32_t) * h->K, cudaMemcpyDeviceToHost, h->stream));
+  JK_CUDA(h, cudaStreamSynchronize(h->stream));
+  for (int32_t v : st)
+    if (v & JKCALS_BLOCK_NOT_SPD) return fail(JKCALS_ERR_NOT_SPD, "a submodel met a non-SPD Hadamard-of-Grams matrix");
+  return JKCALS_OK;
+}
+
+jkcals_status jkcals_als_sweep(jkcals_t h, int nsweeps, double* losses) {
+  JK_TRY(check_handle(h));
+  if (nsweeps < 0) return fail(JKCALS_ERR_ARG, "nsweeps must be >= 0");
+  if (nsweeps == 0) return JKCALS_OK;
+  JK_TRY(ensure_loss_cap(h, nsweeps));
+  h->tol_host = 0.0;
+  JK_CUDA(h, cudaMemsetAsync(h->d_tol, 0, sizeof(double), h->stream));
+  JK_CUDA(h, cudaMemsetAsync(h->d_sweep_idx, 0, sizeof(int), h->stream));
+  JK_TRY(run_sweeps(h, nsweeps));
+  if (losses != nullptr) JK_TRY(copy_out(h, losses, h->loss_hist, sizeof(double) * nsweeps * h->K));
+  return any_not_spd(h);
+}
+
+jkcals_status jkcals_als_sweep_async(jkcals_t h, int nsweeps, double* losses_dev) {
+  JK_TRY(check_handle(h));
+  if (nsweeps < 0) return fail(JKCALS_ERR_ARG, "nsweeps must be >= 0");
+  if (nsweeps == 0) return JKCALS_OK;
+  if (losses_dev != nullptr && is_host_pointer(losses_dev))
+    return fail(JKCALS_ERR_ARG, "losses_dev must be device memory");
+  JK_TRY(ensure_loss_cap(h, nsweeps));
+  JK_CUDA(h, cudaMemsetAsync(h->d_tol, 0, sizeof(double), h->stream));
+  JK_CUDA(h, cudaMemsetAsync(h->d_sweep_idx, 0, sizeof(int), h->stream));
+  JK_TRY(run_sweeps(h, nsweeps));
+  if (losses_dev != nullptr)
+    JK_CUDA(h, cudaMemcpyAsync(losses_dev, h->loss_hist, sizeof(double) * nsweeps * h->K,
+                               cudaMemcpyDeviceToDevice, h->stream));
+  return JKCALS_OK;
+}
+
+jkcals_status jkcals_kernel_times(jkcals_t h, double* ms) {
+  JK_TRY(check_handle(h));
+  if (ms == nullptr) return fail(JKCALS_ERR_ARG, "ms is NULL");
+  if (!h->opt.kernel_timing) return fail(JKCALS_ERR_STATE, "kernel_timing was not enabled at create");
+  JK_CUDA(h, cudaStreamSynchronize(h->stream));
+  for (int n = 0; n < h->N; ++n) {
+    float t = 0.f;
+    cudaError_t e = cudaEventElapsedTime(&t, h->ev_start[n], h->ev_stop[n]);
+    if (e == cudaErrorInvalidResourceHandle || e == cudaErrorNotReady) {
+      cudaGetLastError();
+      return fail(JKCALS_ERR_STATE, "no completed sweep to time yet");
+    }
+    JK_CUDA(h, e);
+    ms[n] = (double)t;
+  }
+  return JKCALS_OK;
+}
+
+jkcals_status jkcals_sweep_info(jkcals_t h, int* kernels_per_sweep, int* splits) {
+  JK_TRY(check_handle(h));
+  if (kernels_per_sweep == nullptr) return fail(JKCALS_ERR_ARG, "kernels_per_sweep is NULL");
+  *kernels_per_sweep = h->kernels_per_sweep;
+  if (splits)
+    for (int n = 0; n < h->N; ++n) splits[n] = h->plan[n].splits;
+  return JKCALS_OK;
+}
+
+jkcals_status jkcals_run(jkcals_t h, int max_sweeps, double tol, int* sweeps_done, double* final_loss) {
+  JK_TRY(check_handle(h));
+  if (max_sweeps < 0 || !(tol >= 0.0)) return fail(JKCALS_ERR_ARG, "bad max_sweeps or tol");
+  const int chunk = 16;
+  JK_TRY(ensure_loss_cap(h, chunk));
+  h->tol_host = tol;
+  JK_CUDA(h, cudaMemcpyAsync(h->d_tol, &h->tol_host, sizeof(double), cudaMemcpyHostToDevice, h->stream));
+  int done = 0;
+  std::vector<int32_t> st(h->K);
+  while (done < max_sweeps) {
+    const int n = std::min(chunk, max_sweeps - done);
+    JK_CUDA(h, cudaMemsetAsync(h->d_sweep_idx, 0, sizeof(int), h->stream));
+    JK_TRY(run_sweeps(h, n));
+    done += n;
+    JK_CUDA(h, cudaMemcpyAsync(st.data(), h->d_status, sizeof(int32_t) * h->K, cudaMemcpyDeviceToHost, h->stream));
+    JK_CUDA(h, cudaStreamSynchronize(h->stream));
+    bool all_frozen = true;
+    for (int32_t v : st) all_frozen = all_frozen && (v != 0);
+    if (all_frozen) break;
+  }
+  h->tol_host = 0.0;
+  JK_CUDA(h, cudaMemsetAsync(h->d_tol, 0, sizeof(double), h->stream));
+  if (sweeps_done) *sweeps_done = done;
+  if (final_loss) JK_TRY(copy_out(h, final_loss, h->d_loss_last, sizeof(double) * h->K));
+  return any_not_spd(h);
+}
+
+jkcals_status jkcals_get_factors(jkcals_t h, double* const* U) {
+  JK_TRY(check_handle(h));
+  if (U == nullptr) return fail(JKCALS_ERR_ARG, "U is NULL");
+  for (int n = 0; n < h->N; ++n)
+    if (U[n] == nullptr) return fail(JKCALS_ERR_ARG, "U[n] is NULL");
+  for (int n = 0; n < h->N; ++n)
+    JK_CUDA(h, cudaMemcpyAsync(U[n], h->U[n], sizeof(double) * h->dims[n] * h->C, cudaMemcpyDefault, h->stream));
+  JK_CUDA(h, cudaStreamSynchronize(h->stream));
+  return JKCALS_OK;
+}
+
+jkcals_status jkcals_set_factors(jkcals_t h, const double* const* U) {
+  JK_TRY(check_handle(h));
+  if (U == nullptr) return fail(JKCALS_ERR_ARG, "U is NULL");
+  for (int n = 0; n < h->N; ++n)
+    if (U[n] == nullptr) return fail(JKCALS_ERR_ARG, "U[n] is NULL");
+  for (int n = 0; n < h->N; ++n)
+    JK_CUDA(h, cudaMemcpyAsync(h->U[n], U[n], sizeof(double) * h->dims[n] * h->C, cudaMemcpyDefault, h->stream));
+  JK_TRY(refresh_factor_state(h));
+  JK_CUDA(h, cudaStreamSynchronize(h->stream));
+  return JKCALS_OK;
+}
+
+jkcals_status jkcals_get_block_status(jkcals_t h, int32_t* status) {
+  JK_TRY(check_handle(h));
+  if (status == nullptr) return fail(JKCALS_ERR_ARG, "status is NULL");
+  JK_CUDA(h, cudaMemcpyAsync(status, h->d_status, sizeof(int32_t) * h->K, cudaMemcpyDefault, h->stream));
+  JK_CUDA(h, cudaStreamSynchronize(h->stream));
+  return JKCALS_OK;
+}
+
+jkcals_status jkcals_grad(jkcals_t h, const double* const* U, double* const* G, double* loss) {
+  JK_TRY(check_handle(h));
+  if (U != nullptr)
+    for (int n = 0; n < h->N; ++n)
+      if (U[n] == nullptr) return fail(JKCALS_ERR_ARG, "U[n] is NULL");
+  return grad_impl(h, U, G, loss);
+}
+
+jkcals_status jkcals_sync(jkcals_t h) {
+  JK_TRY(check_handle(h));
+  JK_CUDA(h, cudaStreamSynchronize(h->stream));
+  return JKCALS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,195 @@
+// Internal declarations shared by the translation units of libjkcals.so.
+//
+// Device data layout (one handle):
+//   Tn64[n]   FP64 mode-n unfolding T_(n), I_n x J_n row-major, columns in the
+//             order of Eq. kolda_mapping (lowest other mode fastest)       [FP64 form]
+//   U[n]      FP64 multi-matrix Ubar^(n), I_n x C row-major
+//   gram[n]   FP64 Grams G^(n)_g = Ubar^(n)_{|g}^T Ubar^(n)_{|g}, block g at gram_off[g]
+//             (R_g x R_g row-major, packed one block after another)
+//   part      split-K partial MTTKRPs, S x I_n x C (FP64 or FP32 by form)
+//   gpart     per (block, row chunk) partial Grams, K x RC x 32 x 32 FP64
+//   fpart     per (block, row chunk) partial sum(U_N * M_N), K x RC FP64
+//   normT2    ||T_{-g}||^2 per block, FP64
+//   status    per-block status bits (JKCALS_BLOCK_*)
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/jkcals.h"
+
+namespace jk {
+
+constexpr int kMaxModes = 8;
+constexpr int kMaxRank = 32;
+
+// Metadata of the blocks, device side.
+struct BlockMeta {
+  const int* R;          // K
+  const int* off;        // K: first column of block g
+  const int* gram_off;   // K: offset of block g's R_g x R_g Gram
+  const int64_t* lo_ptr; // K+1
+  const int64_t* lo_idx; // left-out sample indices (sorted within a block)
+};
+
+// Factor operands of the on-the-fly Khatri-Rao product of one mode.
+struct KrpOperands {
+  const double* U[kMaxModes - 1];  // other modes in increasing mode order
+  int dims[kMaxModes - 1];         // their sizes
+  int nother;                      // N - 1
+};
+
+// Row-chunk plan of the update kernels for one mode.
+struct UpdatePlan {
+  int rows_per_chunk;
+  int RC;
+};
+
+struct ModePlan {
+  int splits;          // split-K factor of the MTTKRP
+  int64_t kchunk;      // columns of T_(n) per split
+  UpdatePlan upd;
+};
+
+}  // namespace jk
+
+struct jkcals_ctx {
+  int N = 0;
+  int64_t dims[jk::kMaxModes] = {0};
+  int64_t J[jk::kMaxModes] = {0};
+  int n_hat = 0;
+  int K = 0;
+  int C = 0;
+  int Rmax = 0;
+  jkcals_options opt{};
+  cudaStream_t stream = nullptr;
+  bool owns_stream = false;
+  int device = 0;
+  int num_sms = 0;
+  bool broken = false;
+  int64_t bytes_allocated = 0;
+  std::vector<void*> allocations;
+
+  std::vector<int> R, off, gram_off;
+  std::vector<int64_t> lo_ptr, lo_idx;
+  int gram_total = 0;  // sum R_g^2
+
+  // device metadata
+  int* d_R = nullptr;
+  int* d_off = nullptr;
+  int* d_gram_off = nullptr;
+  int64_t* d_lo_ptr = nullptr;
+  int64_t* d_lo_idx = nullptr;
+  int32_t* d_status = nullptr;
+  double* d_normT2 = nullptr;
+  double* d_loss_prev = nullptr;
+  double* d_loss_last = nullptr;
+  double* d_tol = nullptr;
+  int* d_sweep_idx = nullptr;
+
+  // tensor copies and factors
+  double* Tn64[jk::kMaxModes] = {nullptr};
+  double* U[jk::kMaxModes] = {nullptr};
+  double* gram[jk::kMaxModes] = {nullptr};
+
+  // workspace
+  void* part = nullptr;
+  size_t part_bytes = 0;
+  double* gpart = nullptr;
+  double* fpart = nullptr;
+  size_t upd_chunks = 0;  // capacity K * RC_max
+  double* mbuf = nullptr; // I_max x C FP64 scratch for jkcals_mttkrp / grad
+  double* loss_hist = nullptr;
+  int loss_cap = 0;
+
+  jk::ModePlan plan[jk::kMaxModes];
+
+  // gradient state (allocated on the first jkcals_grad)
+  bool grad_ready = false;
+  double* gU[jk::kMaxModes] = {nullptr};
+  double* ggram[jk::kMaxModes] = {nullptr};
+  double* gG[jk::kMaxModes] = {nullptr};
+  double* geg = nullptr;  // K per-block losses + their sum
+
+  double tol_host = 0.0;
+
+  cudaGraphExec_t sweep_exec = nullptr;
+  bool graph_valid = false;
+
+  // kernel timing (opt.kernel_timing): events around each mode's MTTKRP
+  cudaEvent_t ev_start[jk::kMaxModes] = {nullptr};
+  cudaEvent_t ev_stop[jk::kMaxModes] = {nullptr};
+  int kernels_per_sweep = 0;
+};
+
+namespace jk {
+
+// ---- error plumbing (jk_capi.cu) --------------------------------------------
+void set_error(const std::string& msg);
+
+// ---- create-time preparation (jk_prep.cu) -----------------------------------
+// T_(n) in Kolda column order from a dense C-order FP64 tensor on the device.
+cudaError_t launch_unfold_f64(const double* Tc, const int64_t* dims, int N, int n, double* out,
+                              cudaStream_t s);
+// Convert an FP32 device buffer to FP64.
+cudaError_t launch_f32_to_f64(const float* in, double* out, int64_t count, cudaStream_t s);
+// slice[i] = sum_j T_(n)(i, j)^2 for the I rows of an unfolding.
+cudaError_t launch_row_sumsq(const double* Tn, int64_t I, int64_t J, double* out, cudaStream_t s);
+// normT2[g] = sum over i not in D_g of slice[i].
+cudaError_t launch_block_norms(const double* slice, int64_t I, int K, BlockMeta bm, double* normT2,
+                               cudaStream_t s);
+// Zero rows D_g of block g of the sampled mode's multi-matrix.
+cudaError_t launch_zero_left_out(double* U, int C, int K, BlockMeta bm, cudaStream_t s);
+// G^(n)_g for every block of one mode.
+cudaError_t launch_grams(const double* U, int64_t I, int C, int K, BlockMeta bm, double* gram,
+                         cudaStream_t s);
+
+// ---- concurrent MTTKRP, FP64 CUDA-core form (jk_mttkrp_f64.cu) --------------
+cudaError_t launch_mttkrp_f64(const double* Tn, int64_t I, int64_t J, int C, const KrpOperands& kr,
+                              int splits, int64_t kchunk, double* part, cudaStream_t s);
+// out = sum_{s < S} part[s] (fixed order), count elements.
+cudaError_t launch_reduce_partials_f64(const double* part, int S, int64_t count, double* out,
+                                       cudaStream_t s);
+
+// ---- per-block update (jk_update.cu) ----------------------------------------
+struct UpdateArgs {
+  int N, n, n_hat, K, C;
+  int64_t I;
+  BlockMeta bm;
+  double* U;                        // Ubar^(n), written
+  const double* gram[kMaxModes];    // Grams of every mode (gram[n] written in phase B)
+  double* gram_n;
+  const void* part;                 // S x I x C partial MTTKRPs
+  int part_is_f32;
+  int S;
+  int rows_per_chunk, RC;
+  double* gpart;
+  double* fpart;
+  int32_t* status;
+  int normalise;
+  const double* normT2;
+  double* loss_prev;
+  double* loss_last;
+  const double* tol;                // device scalar
+  double* loss_hist;                // NULL or cap x K
+  int loss_cap;
+  const int* sweep_idx;             // device scalar
+};
+cudaError_t launch_update(const UpdateArgs& a, cudaStream_t s);
+cudaError_t launch_advance_sweep(int* sweep_idx, cudaStream_t s);
+
+// ---- gradient epilogue (jk_update.cu) ----------------------------------------
+// G_n(i, c) = 2 (U_n H_n - M_n)(i, c) per block, rows D_g of the sampled mode set to 0.
+cudaError_t launch_grad_epilogue(int N, int n, int n_hat, int64_t I, int C, int K, BlockMeta bm,
+                                 const double* U, const double* const* gram, const double* M,
+                                 double* G, cudaStream_t s);
+// eg[g] = ||T_{-g}||^2 + sum(*_k G^(k)_g) - 2 sum(U_{N-1|g} * M_{N-1|g}) for every block,
+// eg[K] = sum_g eg[g] (fixed order).  M is the last mode's concurrent MTTKRP.
+cudaError_t launch_grad_loss(int N, int64_t I, int C, int K, BlockMeta bm, const double* U,
+                             const double* const* gram, const double* M, const double* normT2,
+                             double* eg, cudaStream_t s);
+
+}  // namespace jk
