@@ -205,9 +205,9 @@ jkcals_status enqueue_mttkrp(jkcals_ctx* h, int n, double* const* U) {
 jkcals_status enqueue_sweep(jkcals_ctx* h) {
   int kernels = 0;
   for (int n = 0; n < h->N; ++n) {
-    if (h->opt.kernel_timing) JK_CUDA(h, cudaEventRecord(h->ev_start[n], h->stream));
+    if (h->opt.kernel_timing) JK_CUDA(h, cudaEventRecordWithFlags(h->ev_start[n], h->stream, cudaEventRecordExternal));
     JK_TRY(enqueue_mttkrp(h, n, h->U));
-    if (h->opt.kernel_timing) JK_CUDA(h, cudaEventRecord(h->ev_stop[n], h->stream));
+    if (h->opt.kernel_timing) JK_CUDA(h, cudaEventRecordWithFlags(h->ev_stop[n], h->stream, cudaEventRecordExternal));
     UpdateArgs a = update_args(h, n, h->part, 0, h->plan[n].splits);
     JK_CUDA(h, launch_update(a, h->stream));
     kernels += 3;
