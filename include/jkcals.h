@@ -206,6 +206,45 @@ jkcals_status jkcals_grad(jkcals_t h, const double* const* U, double* const* G, 
 /* Block until the handle's stream is idle. */
 jkcals_status jkcals_sync(jkcals_t h);
 
+/*
+ * jkcals_mttkrp_f64_noalloc -- the FP64 concurrent MTTKRP of one mode for callers
+ * that cannot allocate device memory.  The paper has no counterpart: it is a
+ * deployment variant of the same computation as jkcals_mttkrp.  Callers such as
+ * a solver that runs inside someone else's memory pool or arena, a step whose
+ * memory budget was fixed in advance, or a latency-critical loop in which a
+ * cudaMalloc would synchronise the device cannot create a handle, because a
+ * handle allocates its own tensor copies and workspace.  This entry point
+ * allocates nothing: the caller passes every input and the output, and the
+ * split-K partial sums go to a fixed scratch array that the library keeps in
+ * device memory.
+ *
+ *   M_out = Tn (U[N-1] (.) ... (.) U[mode+1] (.) U[mode-1] (.) ... (.) U[0])
+ *
+ *  N, dims  order (2..8) and the N dims (host)
+ *  mode     the mode whose MTTKRP is computed
+ *  Tn       device, I_mode x J row-major FP64 with J = prod_{k != mode} dims[k]:
+ *           the mode-`mode` unfolding, column j holding the element whose other
+ *           indices satisfy j = sum_{k != mode} i_k prod_{m < k, m != mode} dims[m]
+ *  U        N pointers (host array) to device I_k x C row-major FP64 matrices;
+ *           U[mode] is not read and may be NULL
+ *  C        columns of every U[k] and of M_out
+ *  M_out    device, I_mode x C row-major FP64, overwritten
+ *  stream   cudaStream_t as void*, NULL = legacy default stream
+ *
+ * Scratch: a file-scope device array of 2^21 doubles (16 MiB), which every GPU
+ * that loads the library holds until the process exits.  Calls with
+ * dims[mode] * C > 2^21 return JKCALS_ERR_UNSUPPORTED.  The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress, no
+ * allocation); make that first call before any stream capture.  Every call
+ * shares the array and overwrites, before reading, every element it uses, so
+ * the previous call's leftovers never matter; but calls whose work overlaps on
+ * the GPU (other streams, other host threads) race on the array and give wrong
+ * results: serialise them, e.g. on one stream.  Host pointers for Tn, U[k] or
+ * M_out are rejected with JKCALS_ERR_ARG.  Returns after enqueueing (no sync).
+ */
+jkcals_status jkcals_mttkrp_f64_noalloc(int N, const int64_t* dims, int mode, const double* Tn,
+                                        const double* const* U, int C, double* M_out, void* stream);
+
 /* Thread-local message of the last failing call ("" if none). */
 const char* jkcals_last_error(void);
 

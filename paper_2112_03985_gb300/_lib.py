@@ -43,6 +43,7 @@ SIGNATURES = {
     "jkcals_get_block_status": (ct.c_int, [P, I32P]),
     "jkcals_grad": (ct.c_int, [P, PP, PP, P]),
     "jkcals_sync": (ct.c_int, [P]),
+    "jkcals_mttkrp_f64_noalloc": (ct.c_int, [ct.c_int, I64P, ct.c_int, P, PP, ct.c_int, P, P]),
     "jkcals_last_error": (ct.c_char_p, []),
     "jkcals_version": (ct.c_char_p, []),
 }

@@ -217,3 +217,22 @@ def from_workload(w, precision: str = "fp64", device: Optional[str] = None, **kw
         T = torch.from_numpy(T).to(device)
         init = [torch.from_numpy(u).to(device) for u in init]
     return JKCALS(T, w.n_hat, w.ranks, w.left_out, init, precision=precision, **kw)
+
+
+def mttkrp_f64_noalloc(Tn, U, mode: int, out, stream=None):
+    """FP64 concurrent MTTKRP of one mode without any device allocation
+    (jkcals_mttkrp_f64_noalloc): Tn is the I_mode x J unfolding, U the N factor
+    matrices (I_k x C), out the I_mode x C result; all CUDA tensors.  Enqueued
+    on ``stream`` (default: torch's current stream), not synchronised."""
+    lib = L.load()
+    N = len(U)
+    dims = [int(u.shape[0]) for u in U]
+    C = int(U[(mode + 1) % N].shape[1])
+    d = (ct.c_int64 * N)(*dims)
+    ptrs = (ct.c_void_p * N)(*[(_ptr(u) if (k != mode and u is not None) else None) for k, u in enumerate(U)])
+    if stream is None:
+        stream = _torch().cuda.current_stream().cuda_stream
+    L.check(lib.jkcals_mttkrp_f64_noalloc(N, d, int(mode), ct.c_void_p(_ptr(Tn)), ptrs, C,
+                                          ct.c_void_p(_ptr(out)), ct.c_void_p(stream)),
+            "jkcals_mttkrp_f64_noalloc")
+    return out
