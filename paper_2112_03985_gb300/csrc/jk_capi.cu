@@ -9,7 +9,10 @@
 #include <string>
 #include <vector>
 
+#include <cudaTypedefs.h>
+
 #include "jk_common.cuh"
+#include "jk_tc.cuh"
 
 namespace jk {
 thread_local std::string g_last_error;
@@ -146,6 +149,72 @@ void make_plan(jkcals_ctx* h) {
   }
 }
 
+int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+
+// Tensor-core plan of every mode: N tile, split-K factor, pipeline depth.
+jkcals_status make_tc_plan(jkcals_ctx* h) {
+  const int prec = h->opt.precision;
+  const int nsplit = tc::form_nsplit(prec), bk = tc::form_bk(prec), chunk = tc::form_chunk(prec);
+  const int bn_max = nsplit >= 3 ? 160 : 256;
+  for (int n = 0; n < h->N; ++n) {
+    TcModePlan& p = h->tcplan[n];
+    const int64_t I = h->dims[n];
+    p.nsplit = nsplit;
+    p.a_mode = (n == 0) ? 1 : 0;
+    p.Ia_pad = (int)round_up(h->dims[p.a_mode], chunk);
+    p.Jp = (int64_t)p.Ia_pad * (h->J[n] / h->dims[p.a_mode]);
+    const int64_t nt = (I + bn_max - 1) / bn_max;
+    p.BN = (int)round_up((I + nt - 1) / nt, 16);
+    p.tiles_c = (h->C + 127) / 128;
+    p.tiles_n = (int)((I + p.BN - 1) / p.BN);
+    const size_t stage = (size_t)nsplit * (128 * 128 + (size_t)p.BN * 128);
+    const size_t budget = 227 * 1024 - 2048;
+    p.stages = (int)std::min<size_t>(4, budget / stage);
+    if (p.stages < 2) return fail(JKCALS_ERR_UNSUPPORTED, "tensor-core tile does not fit shared memory");
+    p.tmem_cols = 32;
+    while (p.tmem_cols < p.BN) p.tmem_cols *= 2;
+    const int64_t base = (int64_t)p.tiles_c * p.tiles_n;
+    const int64_t ksteps = (p.Jp + bk - 1) / bk;
+    int64_t S = h->opt.splits > 0 ? h->opt.splits : std::max<int64_t>(1, h->num_sms / base);
+    if (h->opt.splits <= 0) S = std::min<int64_t>(S, std::max<int64_t>(1, ksteps / 4));
+    S = std::max<int64_t>(1, std::min<int64_t>(S, ksteps));
+    p.kchunk = ((ksteps + S - 1) / S) * bk;
+    p.splits = (int)((p.Jp + p.kchunk - 1) / p.kchunk);
+    if (p.tiles_n > 65535 || p.splits > 65535) return fail(JKCALS_ERR_UNSUPPORTED, "grid too large");
+  }
+  return JKCALS_OK;
+}
+
+jkcals_status encode_tensor_maps(jkcals_ctx* h) {
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  if (encode == nullptr) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || fn == nullptr)
+      return fail(JKCALS_ERR_CUDA, "cuTensorMapEncodeTiled entry point unavailable");
+    encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }
+  const int prec = h->opt.precision;
+  const int eb = tc::form_elem_bytes(prec), bk = tc::form_bk(prec);
+  const CUtensorMapDataType dt = eb == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+  for (int n = 0; n < h->N; ++n) {
+    const TcModePlan& p = h->tcplan[n];
+    for (int part = 0; part < 3; ++part) {
+      void* base = h->Tp[n][part < p.nsplit ? part : 0];
+      cuuint64_t gdim[2] = {(cuuint64_t)p.Jp, (cuuint64_t)h->dims[n]};
+      cuuint64_t gstride[1] = {(cuuint64_t)p.Jp * eb};
+      cuuint32_t box[2] = {(cuuint32_t)bk, (cuuint32_t)p.BN};
+      cuuint32_t estride[2] = {1, 1};
+      CUresult r = encode(&h->tmap[n][part], dt, 2, base, gdim, gstride, box, estride, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                          CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+      if (r != CUDA_SUCCESS) return fail(JKCALS_ERR_CUDA, "cuTensorMapEncodeTiled failed");
+    }
+  }
+  return JKCALS_OK;
+}
+
 jkcals_status ensure_loss_cap(jkcals_ctx* h, int need) {
   if (need <= h->loss_cap) return JKCALS_OK;
   if (h->loss_hist) dfree(h, h->loss_hist);
@@ -190,15 +259,56 @@ UpdateArgs update_args(jkcals_ctx* h, int n, const void* part, int part_is_f32, 
   a.loss_hist = h->loss_hist;
   a.loss_cap = h->loss_cap;
   a.sweep_idx = h->d_sweep_idx;
+  a.UT = h->tc ? h->UT[n] : nullptr;
+  a.I_pad = h->Ipad[n];
   return a;
 }
 
-// Enqueue the concurrent MTTKRP of mode n for factor set U into h->part.
-jkcals_status enqueue_mttkrp(jkcals_ctx* h, int n, double* const* U) {
-  const ModePlan& p = h->plan[n];
-  KrpOperands kr = krp_operands(h, n, U);
-  JK_CUDA(h, launch_mttkrp_f64(h->Tn64[n], h->dims[n], h->J[n], h->C, kr, p.splits, p.kchunk,
-                               static_cast<double*>(h->part), h->stream));
+// Enqueue the concurrent MTTKRP of mode n for factor set (U, UT) into h->part.
+jkcals_status enqueue_mttkrp(jkcals_ctx* h, int n, double* const* U, float* const* UT) {
+  if (!h->tc) {
+    const ModePlan& p = h->plan[n];
+    KrpOperands kr = krp_operands(h, n, U);
+    JK_CUDA(h, launch_mttkrp_f64(h->Tn64[n], h->dims[n], h->J[n], h->C, kr, p.splits, p.kchunk,
+                                 static_cast<double*>(h->part), h->stream));
+    return JKCALS_OK;
+  }
+  const TcModePlan& p = h->tcplan[n];
+  tc::TcPlan tp{p.BN, p.tiles_c, p.tiles_n, p.splits, p.stages, p.tmem_cols, p.nsplit, p.a_mode, p.Ia_pad, p.Jp,
+                p.kchunk};
+  tc::TcArgs a{};
+  a.I = h->dims[n];
+  a.Jp = p.Jp;
+  a.kchunk = p.kchunk;
+  a.C = h->C;
+  a.BN = p.BN;
+  a.tmem_cols = p.tmem_cols;
+  a.stages = p.stages;
+  a.Ia_pad = p.Ia_pad;
+  a.UTa = UT[p.a_mode];
+  int t = 0;
+  for (int k = 0; k < h->N; ++k) {
+    if (k == n || k == p.a_mode) continue;
+    a.qdims[t] = (int)h->dims[k];
+    a.qpad[t] = (int)h->Ipad[k];
+    a.UTq[t] = UT[k];
+    ++t;
+  }
+  a.nq = t;
+  a.part = static_cast<float*>(h->part);
+  a.err = h->d_err;
+  JK_CUDA(h, tc::launch_mttkrp_tc(h->opt.precision, tp, h->tmap[n], a, h->stream));
+  return JKCALS_OK;
+}
+
+int mode_splits(const jkcals_ctx* h, int n) { return h->tc ? h->tcplan[n].splits : h->plan[n].splits; }
+
+jkcals_status reduce_into(jkcals_ctx* h, int n, double* out) {
+  const int64_t cnt = h->dims[n] * (int64_t)h->C;
+  if (h->tc)
+    JK_CUDA(h, launch_reduce_partials_f32(static_cast<float*>(h->part), mode_splits(h, n), cnt, out, h->stream));
+  else
+    JK_CUDA(h, launch_reduce_partials_f64(static_cast<double*>(h->part), mode_splits(h, n), cnt, out, h->stream));
   return JKCALS_OK;
 }
 
@@ -206,9 +316,9 @@ jkcals_status enqueue_sweep(jkcals_ctx* h) {
   int kernels = 0;
   for (int n = 0; n < h->N; ++n) {
     if (h->opt.kernel_timing) JK_CUDA(h, cudaEventRecordWithFlags(h->ev_start[n], h->stream, cudaEventRecordExternal));
-    JK_TRY(enqueue_mttkrp(h, n, h->U));
+    JK_TRY(enqueue_mttkrp(h, n, h->U, h->UT));
     if (h->opt.kernel_timing) JK_CUDA(h, cudaEventRecordWithFlags(h->ev_stop[n], h->stream, cudaEventRecordExternal));
-    UpdateArgs a = update_args(h, n, h->part, 0, h->plan[n].splits);
+    UpdateArgs a = update_args(h, n, h->part, h->tc ? 1 : 0, mode_splits(h, n));
     JK_CUDA(h, launch_update(a, h->stream));
     kernels += 3;
   }
@@ -254,6 +364,9 @@ jkcals_status refresh_factor_state(jkcals_ctx* h) {
   JK_CUDA(h, launch_zero_left_out(h->U[h->n_hat], h->C, h->K, bm, h->stream));
   for (int n = 0; n < h->N; ++n)
     JK_CUDA(h, launch_grams(h->U[n], h->dims[n], h->C, h->K, bm, h->gram[n], h->stream));
+  if (h->tc)
+    for (int n = 0; n < h->N; ++n)
+      JK_CUDA(h, tc::launch_factor_to_ut(h->U[n], h->dims[n], h->C, h->UT[n], h->Ipad[n], h->stream));
   JK_CUDA(h, cudaMemsetAsync(h->d_status, 0, sizeof(int32_t) * h->K, h->stream));
   JK_CUDA(h, cudaMemsetAsync(h->d_loss_prev, 0xff, sizeof(double) * h->K, h->stream));
   JK_CUDA(h, cudaMemsetAsync(h->d_loss_last, 0xff, sizeof(double) * h->K, h->stream));
@@ -263,6 +376,20 @@ jkcals_status refresh_factor_state(jkcals_ctx* h) {
 jkcals_status copy_out(jkcals_ctx* h, void* dst, const void* src, size_t bytes) {
   JK_CUDA(h, cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, h->stream));
   if (is_host_pointer(dst)) JK_CUDA(h, cudaStreamSynchronize(h->stream));
+  return JKCALS_OK;
+}
+
+// Reads the tensor-core kernel's error word (set when a bounded wait expired).
+jkcals_status check_device_error(jkcals_ctx* h) {
+  if (!h->tc || h->d_err == nullptr) return JKCALS_OK;
+  int err = 0;
+  JK_CUDA(h, cudaMemcpyAsync(&err, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  JK_CUDA(h, cudaStreamSynchronize(h->stream));
+  if (err != 0) {
+    JK_CUDA(h, cudaMemsetAsync(h->d_err, 0, sizeof(int), h->stream));
+    return fail(JKCALS_ERR_TIMEOUT, "a bounded wait in the tensor-core MTTKRP expired (code " +
+                                        std::to_string(err) + "); results of that call are invalid");
+  }
   return JKCALS_OK;
 }
 
@@ -370,6 +497,42 @@ jkcals_status create_impl(jkcals_ctx* h, const void* T, int T_dtype, const int32
   dfree(h, slice);
   dfree(h, Tc);
 
+  // tensor-core forms: padded, precision-split unfoldings replace the FP64 ones
+  if (h->tc) {
+    JK_TRY(make_tc_plan(h));
+    const int eb = tc::form_elem_bytes(h->opt.precision);
+    const int chunk = tc::form_chunk(h->opt.precision);
+    for (int n = 0; n < N; ++n) {
+      const TcModePlan& p = h->tcplan[n];
+      void* parts[3] = {nullptr, nullptr, nullptr};
+      for (int q = 0; q < p.nsplit; ++q) {
+        JK_TRY(dalloc(h, &h->Tp[n][q], (size_t)h->dims[n] * p.Jp * eb));
+        parts[q] = h->Tp[n][q];
+      }
+      JK_CUDA(h, tc::launch_split_unfold(h->opt.precision, h->Tn64[n], h->dims[n], h->J[n],
+                                         h->dims[p.a_mode], p.Ia_pad, p.Jp, parts, st));
+      h->Ipad[n] = round_up(h->dims[n], chunk);
+    }
+    JK_CUDA(h, cudaStreamSynchronize(st));
+    for (int n = 0; n < N; ++n) {
+      dfree(h, h->Tn64[n]);
+      h->Tn64[n] = nullptr;
+      JK_TRY(dalloc_t(h, &h->UT[n], (size_t)h->C * h->Ipad[n]));
+      JK_CUDA(h, cudaMemsetAsync(h->UT[n], 0, sizeof(float) * h->C * h->Ipad[n], st));
+    }
+    JK_TRY(encode_tensor_maps(h));
+    size_t smem = 0;
+    for (int n = 0; n < N; ++n) {
+      const TcModePlan& p = h->tcplan[n];
+      tc::TcPlan tp{p.BN, p.tiles_c, p.tiles_n, p.splits, p.stages, p.tmem_cols, p.nsplit, p.a_mode, p.Ia_pad,
+                    p.Jp, p.kchunk};
+      smem = std::max(smem, tc::tc_smem_bytes(tp));
+    }
+    JK_CUDA(h, tc::prepare_mttkrp_tc(h->opt.precision, smem));
+    JK_TRY(dalloc_t(h, &h->d_err, 1));
+    JK_CUDA(h, cudaMemsetAsync(h->d_err, 0, sizeof(int), st));
+  }
+
   // factors and Grams
   int64_t Imax = 0;
   for (int n = 0; n < N; ++n) {
@@ -381,11 +544,14 @@ jkcals_status create_impl(jkcals_ctx* h, const void* T, int T_dtype, const int32
 
   // plan + workspace
   make_plan(h);
-  size_t part_elems = 0, chunks = 0;
+  size_t part_bytes = 0, chunks = 0;
   for (int n = 0; n < N; ++n) {
-    part_elems = std::max(part_elems, (size_t)h->plan[n].splits * h->dims[n] * h->C);
+    const size_t pb = h->tc ? (size_t)h->tcplan[n].splits * h->dims[n] * h->C * sizeof(float)
+                            : (size_t)h->plan[n].splits * h->dims[n] * h->C * sizeof(double);
+    part_bytes = std::max(part_bytes, pb);
     chunks = std::max(chunks, (size_t)h->plan[n].upd.RC * K);
   }
+  size_t part_elems = part_bytes / sizeof(double) + 1;
   h->part_bytes = part_elems * sizeof(double);
   JK_TRY(dalloc(h, &h->part, h->part_bytes));
   JK_TRY(dalloc_t(h, &h->gpart, chunks * kMaxRank * kMaxRank));
@@ -415,6 +581,12 @@ jkcals_status grad_impl(jkcals_ctx* h, const double* const* U, double* const* G,
       JK_TRY(dalloc_t(h, &h->gG[n], (size_t)h->dims[n] * h->C));
     }
     JK_TRY(dalloc_t(h, &h->geg, (size_t)h->K + 1));
+    if (h->tc) {
+      for (int n = 0; n < N; ++n) {
+        JK_TRY(dalloc_t(h, &h->gUT[n], (size_t)h->C * h->Ipad[n]));
+        JK_CUDA(h, cudaMemsetAsync(h->gUT[n], 0, sizeof(float) * h->C * h->Ipad[n], st));
+      }
+    }
     h->grad_ready = true;
   }
   BlockMeta bm = block_meta(h);
@@ -423,12 +595,14 @@ jkcals_status grad_impl(jkcals_ctx* h, const double* const* U, double* const* G,
     JK_CUDA(h, cudaMemcpyAsync(h->gU[n], src, sizeof(double) * h->dims[n] * h->C, cudaMemcpyDefault, st));
   }
   JK_CUDA(h, launch_zero_left_out(h->gU[h->n_hat], h->C, h->K, bm, st));
-  for (int n = 0; n < N; ++n)
-    JK_CUDA(h, launch_grams(h->gU[n], h->dims[n], h->C, h->K, bm, h->ggram[n], st));
   for (int n = 0; n < N; ++n) {
-    JK_TRY(enqueue_mttkrp(h, n, h->gU));
+    JK_CUDA(h, launch_grams(h->gU[n], h->dims[n], h->C, h->K, bm, h->ggram[n], st));
+    if (h->tc) JK_CUDA(h, tc::launch_factor_to_ut(h->gU[n], h->dims[n], h->C, h->gUT[n], h->Ipad[n], st));
+  }
+  for (int n = 0; n < N; ++n) {
+    JK_TRY(enqueue_mttkrp(h, n, h->gU, h->gUT));
     const int64_t cnt = h->dims[n] * (int64_t)h->C;
-    JK_CUDA(h, launch_reduce_partials_f64(static_cast<double*>(h->part), h->plan[n].splits, cnt, h->mbuf, st));
+    JK_TRY(reduce_into(h, n, h->mbuf));
     if (G != nullptr && G[n] != nullptr) {
       JK_CUDA(h, launch_grad_epilogue(N, n, h->n_hat, h->dims[n], h->C, h->K, bm, h->gU[n], h->ggram,
                                       h->mbuf, h->gG[n], st));
@@ -442,7 +616,7 @@ jkcals_status grad_impl(jkcals_ctx* h, const double* const* U, double* const* G,
     JK_CUDA(h, cudaMemcpyAsync(loss, h->geg + h->K, sizeof(double), cudaMemcpyDefault, st));
   }
   JK_CUDA(h, cudaStreamSynchronize(st));
-  return JKCALS_OK;
+  return check_device_error(h);
 }
 
 }  // namespace
@@ -512,8 +686,7 @@ jkcals_status jkcals_create(jkcals_t* out, int N, const int64_t* dims, const voi
   jkcals_options o;
   jkcals_default_options(&o);
   if (opt) o = *opt;
-  if (o.precision != JKCALS_FP64)
-    return fail(JKCALS_ERR_UNSUPPORTED, "precision form not built in this library version");
+  if (o.precision < JKCALS_FP64 || o.precision > JKCALS_SPLIT_BF16) return fail(JKCALS_ERR_ARG, "bad precision");
   if (o.splits < 0) return fail(JKCALS_ERR_ARG, "splits must be >= 0");
 
   jkcals_ctx* h = new jkcals_ctx();
@@ -522,6 +695,7 @@ jkcals_status jkcals_create(jkcals_t* out, int N, const int64_t* dims, const voi
   h->n_hat = sampled_mode;
   h->K = K;
   h->opt = o;
+  h->tc = (o.precision != JKCALS_FP64);
   cudaError_t e = cudaGetDevice(&h->device);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
   if (e != cudaSuccess) {
@@ -557,14 +731,15 @@ jkcals_status jkcals_mttkrp(jkcals_t h, int mode, double* M_out) {
   JK_TRY(check_handle(h));
   if (mode < 0 || mode >= h->N) return fail(JKCALS_ERR_ARG, "mode out of range");
   if (M_out == nullptr) return fail(JKCALS_ERR_ARG, "M_out is NULL");
-  JK_TRY(enqueue_mttkrp(h, mode, h->U));
+  JK_TRY(enqueue_mttkrp(h, mode, h->U, h->UT));
   const int64_t cnt = h->dims[mode] * (int64_t)h->C;
-  JK_CUDA(h, launch_reduce_partials_f64(static_cast<double*>(h->part), h->plan[mode].splits, cnt, h->mbuf,
-                                        h->stream));
-  return copy_out(h, M_out, h->mbuf, sizeof(double) * cnt);
+  JK_TRY(reduce_into(h, mode, h->mbuf));
+  JK_TRY(copy_out(h, M_out, h->mbuf, sizeof(double) * cnt));
+  return check_device_error(h);
 }
 
 static jkcals_status any_not_spd(jkcals_ctx* h) {
+  JK_TRY(check_device_error(h));
   std::vector<int32_t> st(h->K);
   JK_CUDA(h, cudaMemcpyAsync(st.data(), h->d_status, sizeof(int32_t) * h->K, cudaMemcpyDeviceToHost, h->stream));
   JK_CUDA(h, cudaStreamSynchronize(h->stream));
@@ -625,7 +800,7 @@ jkcals_status jkcals_sweep_info(jkcals_t h, int* kernels_per_sweep, int* splits)
   if (kernels_per_sweep == nullptr) return fail(JKCALS_ERR_ARG, "kernels_per_sweep is NULL");
   *kernels_per_sweep = h->kernels_per_sweep;
   if (splits)
-    for (int n = 0; n < h->N; ++n) splits[n] = h->plan[n].splits;
+    for (int n = 0; n < h->N; ++n) splits[n] = mode_splits(h, n);
   return JKCALS_OK;
 }
 

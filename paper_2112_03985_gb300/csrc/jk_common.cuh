@@ -13,6 +13,7 @@
 //   status    per-block status bits (JKCALS_BLOCK_*)
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -52,6 +53,12 @@ struct ModePlan {
   int splits;          // split-K factor of the MTTKRP
   int64_t kchunk;      // columns of T_(n) per split
   UpdatePlan upd;
+};
+
+// Tensor-core form of one mode (see jk_tc.cuh).
+struct TcModePlan {
+  int BN, tiles_c, tiles_n, splits, stages, tmem_cols, nsplit, a_mode, Ia_pad;
+  int64_t Jp, kchunk;
 };
 
 }  // namespace jk
@@ -116,6 +123,16 @@ struct jkcals_ctx {
 
   double tol_host = 0.0;
 
+  // tensor-core forms (precision != JKCALS_FP64)
+  bool tc = false;
+  void* Tp[jk::kMaxModes][3] = {{nullptr}};  // split, padded unfoldings
+  float* UT[jk::kMaxModes] = {nullptr};      // C x Ipad FP32 transposed factors
+  float* gUT[jk::kMaxModes] = {nullptr};     // same, for the gradient's factor set
+  int64_t Ipad[jk::kMaxModes] = {0};
+  CUtensorMap tmap[jk::kMaxModes][3];
+  jk::TcModePlan tcplan[jk::kMaxModes];
+  int* d_err = nullptr;                      // bounded-wait expiry code of the TC kernel
+
   cudaGraphExec_t sweep_exec = nullptr;
   bool graph_valid = false;
 
@@ -153,6 +170,9 @@ cudaError_t launch_mttkrp_f64(const double* Tn, int64_t I, int64_t J, int C, con
 // out = sum_{s < S} part[s] (fixed order), count elements.
 cudaError_t launch_reduce_partials_f64(const double* part, int S, int64_t count, double* out,
                                        cudaStream_t s);
+// same for FP32 partials, summed in FP64
+cudaError_t launch_reduce_partials_f32(const float* part, int S, int64_t count, double* out,
+                                       cudaStream_t s);
 
 // ---- per-block update (jk_update.cu) ----------------------------------------
 struct UpdateArgs {
@@ -177,6 +197,8 @@ struct UpdateArgs {
   double* loss_hist;                // NULL or cap x K
   int loss_cap;
   const int* sweep_idx;             // device scalar
+  float* UT;                        // NULL or C x I_pad FP32 transposed copy of Ubar^(n), refreshed
+  int64_t I_pad;
 };
 cudaError_t launch_update(const UpdateArgs& a, cudaStream_t s);
 cudaError_t launch_advance_sweep(int* sweep_idx, cudaStream_t s);

@@ -117,7 +117,26 @@ __global__ void reduce_partials_f64_kernel(const double* __restrict__ part, int 
   }
 }
 
+__global__ void reduce_partials_f32_kernel(const float* __restrict__ part, int S, int64_t count,
+                                           double* __restrict__ out) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < count;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    double acc = (double)part[e];
+    for (int s = 1; s < S; ++s) acc += (double)part[(int64_t)s * count + e];
+    out[e] = acc;
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_reduce_partials_f32(const float* part, int S, int64_t count, double* out,
+                                       cudaStream_t s) {
+  int64_t blocks = (count + 255) / 256;
+  if (blocks > 4096) blocks = 4096;
+  if (blocks < 1) blocks = 1;
+  reduce_partials_f32_kernel<<<(unsigned)blocks, 256, 0, s>>>(part, S, count, out);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_mttkrp_f64(const double* Tn, int64_t I, int64_t J, int C, const KrpOperands& kr,
                               int splits, int64_t kchunk, double* part, cudaStream_t s) {

@@ -220,6 +220,14 @@ __global__ void __launch_bounds__(NTB) update_phase_b(UpdateArgs a) {
     __syncthreads();
   }
   for (int p = tid; p < R * R; p += NTB) a.gram_n[go + p] = G[p / R][p % R];
+  if (a.UT != nullptr) {
+    // FP32 transposed copy for the tensor-core MTTKRP: UT[c][i], i fastest
+    for (int64_t t = tid; t < a.I * R; t += NTB) {
+      const int r = (int)(t / a.I);
+      const int64_t i = t - (int64_t)r * a.I;
+      a.UT[(int64_t)(off + r) * a.I_pad + i] = (float)a.U[i * a.C + off + r];
+    }
+  }
   if (!last) return;
 
   // e_g = ||T_{-g}||^2 + sum(H * G) - 2 sum(U * M)
