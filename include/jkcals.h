@@ -62,7 +62,13 @@ typedef enum {
   JKCALS_TF32 = 1,        /* tcgen05 kind::tf32, FP32 accumulation in TMEM             */
   JKCALS_3XTF32 = 2,      /* hi*hi + hi*lo + lo*hi TF32 products, FP32 accumulation    */
   JKCALS_BF16 = 3,        /* tcgen05 kind::f16 with BF16 operands, FP32 accumulation   */
-  JKCALS_SPLIT_BF16 = 4   /* BF16 hi/mid/lo split, 6 cross products, FP32 accumulation */
+  JKCALS_SPLIT_BF16 = 4,  /* BF16 hi/mid/lo split, 6 cross products, FP32 accumulation */
+  JKCALS_EXACT_BF16 = 5   /* exact-chain sliced BF16: every operand row is cut into four
+                             7-bit integer slices on a shared power-of-two grid, stored as
+                             BF16; the two leading product levels accumulate exactly in
+                             FP32 TMEM (chains <= 1024 terms), the rest in a third
+                             accumulator; chains are combined in FP64.  About FP64-level
+                             MTTKRP accuracy on the tensor cores (10 BF16 MMA passes). */
 } jkcals_prec;
 
 typedef enum { JKCALS_DTYPE_F32 = 0, JKCALS_DTYPE_F64 = 1 } jkcals_dtype;

@@ -10,7 +10,7 @@ LIB_PATH = os.path.join(_HERE, "libjkcals.so")
 OK, ERR_ARG, ERR_CUDA, ERR_OOM, ERR_NOT_SPD, ERR_TIMEOUT, ERR_STATE, ERR_UNSUPPORTED = range(8)
 STATUS_NAMES = {0: "OK", 1: "ERR_ARG", 2: "ERR_CUDA", 3: "ERR_OOM", 4: "ERR_NOT_SPD",
                 5: "ERR_TIMEOUT", 6: "ERR_STATE", 7: "ERR_UNSUPPORTED"}
-PREC = {"fp64": 0, "tf32": 1, "3xtf32": 2, "bf16": 3, "split_bf16": 4}
+PREC = {"fp64": 0, "tf32": 1, "3xtf32": 2, "bf16": 3, "split_bf16": 4, "exact_bf16": 5}
 DTYPE_F32, DTYPE_F64 = 0, 1
 BLOCK_NOT_SPD, BLOCK_CONVERGED = 1, 2
 

@@ -154,12 +154,16 @@ int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 // Tensor-core plan of every mode: N tile, split-K factor, pipeline depth.
 jkcals_status make_tc_plan(jkcals_ctx* h) {
   const int prec = h->opt.precision;
+  const bool exact = prec == JKCALS_EXACT_BF16;
   const int nsplit = tc::form_nsplit(prec), bk = tc::form_bk(prec), chunk = tc::form_chunk(prec);
-  const int bn_max = nsplit >= 3 ? 160 : 256;
+  const int row = tc::form_row_bytes(prec);
+  const int bn_max = (nsplit >= 3) ? 160 : 256;
+  const int n_acc = exact ? 3 : 1;
   for (int n = 0; n < h->N; ++n) {
-    TcModePlan& p = h->tcplan[n];
+    tc::TcPlan& p = h->tcplan[n];
     const int64_t I = h->dims[n];
     p.nsplit = nsplit;
+    p.row_bytes = row;
     p.a_mode = (n == 0) ? 1 : 0;
     p.Ia_pad = (int)round_up(h->dims[p.a_mode], chunk);
     p.Jp = (int64_t)p.Ia_pad * (h->J[n] / h->dims[p.a_mode]);
@@ -167,18 +171,22 @@ jkcals_status make_tc_plan(jkcals_ctx* h) {
     p.BN = (int)round_up((I + nt - 1) / nt, 16);
     p.tiles_c = (h->C + 127) / 128;
     p.tiles_n = (int)((I + p.BN - 1) / p.BN);
-    const size_t stage = (size_t)nsplit * (128 * 128 + (size_t)p.BN * 128);
+    const size_t stage = (size_t)nsplit * ((size_t)128 * row + (size_t)p.BN * row);
     const size_t budget = 227 * 1024 - 2048;
     p.stages = (int)std::min<size_t>(4, budget / stage);
     if (p.stages < 2) return fail(JKCALS_ERR_UNSUPPORTED, "tensor-core tile does not fit shared memory");
+    p.acc_cols = (int)round_up(p.BN, 32);
     p.tmem_cols = 32;
-    while (p.tmem_cols < p.BN) p.tmem_cols *= 2;
+    while (p.tmem_cols < n_acc * p.acc_cols) p.tmem_cols *= 2;
+    if (p.tmem_cols > 512) return fail(JKCALS_ERR_UNSUPPORTED, "accumulators exceed TMEM");
     const int64_t base = (int64_t)p.tiles_c * p.tiles_n;
     const int64_t ksteps = (p.Jp + bk - 1) / bk;
     int64_t S = h->opt.splits > 0 ? h->opt.splits : std::max<int64_t>(1, h->num_sms / base);
     if (h->opt.splits <= 0) S = std::min<int64_t>(S, std::max<int64_t>(1, ksteps / 4));
     S = std::max<int64_t>(1, std::min<int64_t>(S, ksteps));
-    p.kchunk = ((ksteps + S - 1) / S) * bk;
+    int64_t kchunk = ((ksteps + S - 1) / S) * bk;
+    if (exact) kchunk = std::min<int64_t>(kchunk, tc::kExactChainMax);   // exact chains
+    p.kchunk = kchunk;
     p.splits = (int)((p.Jp + p.kchunk - 1) / p.kchunk);
     if (p.tiles_n > 65535 || p.splits > 65535) return fail(JKCALS_ERR_UNSUPPORTED, "grid too large");
   }
@@ -199,16 +207,16 @@ jkcals_status encode_tensor_maps(jkcals_ctx* h) {
   const int eb = tc::form_elem_bytes(prec), bk = tc::form_bk(prec);
   const CUtensorMapDataType dt = eb == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
   for (int n = 0; n < h->N; ++n) {
-    const TcModePlan& p = h->tcplan[n];
-    for (int part = 0; part < 3; ++part) {
+    const tc::TcPlan& p = h->tcplan[n];
+    const CUtensorMapSwizzle swz = p.row_bytes == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B;
+    for (int part = 0; part < 4; ++part) {
       void* base = h->Tp[n][part < p.nsplit ? part : 0];
       cuuint64_t gdim[2] = {(cuuint64_t)p.Jp, (cuuint64_t)h->dims[n]};
       cuuint64_t gstride[1] = {(cuuint64_t)p.Jp * eb};
       cuuint32_t box[2] = {(cuuint32_t)bk, (cuuint32_t)p.BN};
       cuuint32_t estride[2] = {1, 1};
       CUresult r = encode(&h->tmap[n][part], dt, 2, base, gdim, gstride, box, estride, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                          CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                          swz, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
       if (r != CUDA_SUCCESS) return fail(JKCALS_ERR_CUDA, "cuTensorMapEncodeTiled failed");
     }
   }
@@ -231,7 +239,7 @@ jkcals_status ensure_loss_cap(jkcals_ctx* h, int need) {
   return JKCALS_OK;
 }
 
-UpdateArgs update_args(jkcals_ctx* h, int n, const void* part, int part_is_f32, int S) {
+UpdateArgs update_args(jkcals_ctx* h, int n, const void* part, int part_kind, int S) {
   UpdateArgs a{};
   a.N = h->N;
   a.n = n;
@@ -244,7 +252,7 @@ UpdateArgs update_args(jkcals_ctx* h, int n, const void* part, int part_is_f32, 
   for (int k = 0; k < h->N; ++k) a.gram[k] = h->gram[k];
   a.gram_n = h->gram[n];
   a.part = part;
-  a.part_is_f32 = part_is_f32;
+  a.part_kind = part_kind;
   a.S = S;
   a.rows_per_chunk = h->plan[n].upd.rows_per_chunk;
   a.RC = h->plan[n].upd.RC;
@@ -261,11 +269,14 @@ UpdateArgs update_args(jkcals_ctx* h, int n, const void* part, int part_is_f32, 
   a.sweep_idx = h->d_sweep_idx;
   a.UT = h->tc ? h->UT[n] : nullptr;
   a.I_pad = h->Ipad[n];
+  a.cmax = h->tc ? h->cmax[n] : nullptr;
+  a.UT_lo = h->tc ? h->UTlo[n] : nullptr;
   return a;
 }
 
-// Enqueue the concurrent MTTKRP of mode n for factor set (U, UT) into h->part.
-jkcals_status enqueue_mttkrp(jkcals_ctx* h, int n, double* const* U, float* const* UT) {
+// Enqueue the concurrent MTTKRP of mode n for factor set (U, UT, cmax) into h->part.
+jkcals_status enqueue_mttkrp(jkcals_ctx* h, int n, double* const* U, float* const* UT, float* const* UTlo,
+                             float* const* cmax) {
   if (!h->tc) {
     const ModePlan& p = h->plan[n];
     KrpOperands kr = krp_operands(h, n, U);
@@ -273,9 +284,7 @@ jkcals_status enqueue_mttkrp(jkcals_ctx* h, int n, double* const* U, float* cons
                                  static_cast<double*>(h->part), h->stream));
     return JKCALS_OK;
   }
-  const TcModePlan& p = h->tcplan[n];
-  tc::TcPlan tp{p.BN, p.tiles_c, p.tiles_n, p.splits, p.stages, p.tmem_cols, p.nsplit, p.a_mode, p.Ia_pad, p.Jp,
-                p.kchunk};
+  const tc::TcPlan& p = h->tcplan[n];
   tc::TcArgs a{};
   a.I = h->dims[n];
   a.Jp = p.Jp;
@@ -283,29 +292,42 @@ jkcals_status enqueue_mttkrp(jkcals_ctx* h, int n, double* const* U, float* cons
   a.C = h->C;
   a.BN = p.BN;
   a.tmem_cols = p.tmem_cols;
+  a.acc_cols = p.acc_cols;
   a.stages = p.stages;
   a.Ia_pad = p.Ia_pad;
   a.UTa = UT[p.a_mode];
+  a.UTa_lo = UTlo[p.a_mode];
+  a.cmax_a = cmax[p.a_mode];
   int t = 0;
   for (int k = 0; k < h->N; ++k) {
     if (k == n || k == p.a_mode) continue;
     a.qdims[t] = (int)h->dims[k];
     a.qpad[t] = (int)h->Ipad[k];
     a.UTq[t] = UT[k];
+    a.UTq_lo[t] = UTlo[k];
+    a.cmax_q[t] = cmax[k];
     ++t;
   }
   a.nq = t;
   a.part = static_cast<float*>(h->part);
   a.err = h->d_err;
-  JK_CUDA(h, tc::launch_mttkrp_tc(h->opt.precision, tp, h->tmap[n], a, h->stream));
+  a.rowexp = h->rowexp[n];
+  JK_CUDA(h, tc::launch_mttkrp_tc(h->opt.precision, p, h->tmap[n], a, h->stream));
   return JKCALS_OK;
 }
 
 int mode_splits(const jkcals_ctx* h, int n) { return h->tc ? h->tcplan[n].splits : h->plan[n].splits; }
 
+int part_kind(const jkcals_ctx* h) {
+  if (!h->tc) return kPartF64;
+  return h->opt.precision == JKCALS_EXACT_BF16 ? kPartF32x2 : kPartF32;
+}
+
 jkcals_status reduce_into(jkcals_ctx* h, int n, double* out) {
   const int64_t cnt = h->dims[n] * (int64_t)h->C;
-  if (h->tc)
+  if (part_kind(h) == kPartF32x2)
+    JK_CUDA(h, launch_reduce_partials_f32x2(static_cast<float2*>(h->part), mode_splits(h, n), cnt, out, h->stream));
+  else if (part_kind(h) == kPartF32)
     JK_CUDA(h, launch_reduce_partials_f32(static_cast<float*>(h->part), mode_splits(h, n), cnt, out, h->stream));
   else
     JK_CUDA(h, launch_reduce_partials_f64(static_cast<double*>(h->part), mode_splits(h, n), cnt, out, h->stream));
@@ -316,9 +338,9 @@ jkcals_status enqueue_sweep(jkcals_ctx* h) {
   int kernels = 0;
   for (int n = 0; n < h->N; ++n) {
     if (h->opt.kernel_timing) JK_CUDA(h, cudaEventRecordWithFlags(h->ev_start[n], h->stream, cudaEventRecordExternal));
-    JK_TRY(enqueue_mttkrp(h, n, h->U, h->UT));
+    JK_TRY(enqueue_mttkrp(h, n, h->U, h->UT, h->UTlo, h->cmax));
     if (h->opt.kernel_timing) JK_CUDA(h, cudaEventRecordWithFlags(h->ev_stop[n], h->stream, cudaEventRecordExternal));
-    UpdateArgs a = update_args(h, n, h->part, h->tc ? 1 : 0, mode_splits(h, n));
+    UpdateArgs a = update_args(h, n, h->part, part_kind(h), mode_splits(h, n));
     JK_CUDA(h, launch_update(a, h->stream));
     kernels += 3;
   }
@@ -365,8 +387,10 @@ jkcals_status refresh_factor_state(jkcals_ctx* h) {
   for (int n = 0; n < h->N; ++n)
     JK_CUDA(h, launch_grams(h->U[n], h->dims[n], h->C, h->K, bm, h->gram[n], h->stream));
   if (h->tc)
-    for (int n = 0; n < h->N; ++n)
-      JK_CUDA(h, tc::launch_factor_to_ut(h->U[n], h->dims[n], h->C, h->UT[n], h->Ipad[n], h->stream));
+    for (int n = 0; n < h->N; ++n) {
+      JK_CUDA(h, tc::launch_factor_to_ut(h->U[n], h->dims[n], h->C, h->UT[n], h->UTlo[n], h->Ipad[n], h->stream));
+      JK_CUDA(h, tc::launch_colmax(h->UT[n], h->dims[n], h->Ipad[n], h->C, h->cmax[n], h->stream));
+    }
   JK_CUDA(h, cudaMemsetAsync(h->d_status, 0, sizeof(int32_t) * h->K, h->stream));
   JK_CUDA(h, cudaMemsetAsync(h->d_loss_prev, 0xff, sizeof(double) * h->K, h->stream));
   JK_CUDA(h, cudaMemsetAsync(h->d_loss_last, 0xff, sizeof(double) * h->K, h->stream));
@@ -503,14 +527,16 @@ jkcals_status create_impl(jkcals_ctx* h, const void* T, int T_dtype, const int32
     const int eb = tc::form_elem_bytes(h->opt.precision);
     const int chunk = tc::form_chunk(h->opt.precision);
     for (int n = 0; n < N; ++n) {
-      const TcModePlan& p = h->tcplan[n];
-      void* parts[3] = {nullptr, nullptr, nullptr};
+      const tc::TcPlan& p = h->tcplan[n];
+      void* parts[4] = {nullptr, nullptr, nullptr, nullptr};
       for (int q = 0; q < p.nsplit; ++q) {
         JK_TRY(dalloc(h, &h->Tp[n][q], (size_t)h->dims[n] * p.Jp * eb));
         parts[q] = h->Tp[n][q];
       }
+      JK_TRY(dalloc_t(h, &h->rowexp[n], (size_t)h->dims[n]));
+      JK_CUDA(h, tc::launch_row_exponent(h->Tn64[n], h->dims[n], h->J[n], h->rowexp[n], st));
       JK_CUDA(h, tc::launch_split_unfold(h->opt.precision, h->Tn64[n], h->dims[n], h->J[n],
-                                         h->dims[p.a_mode], p.Ia_pad, p.Jp, parts, st));
+                                         h->dims[p.a_mode], p.Ia_pad, p.Jp, h->rowexp[n], parts, st));
       h->Ipad[n] = round_up(h->dims[n], chunk);
     }
     JK_CUDA(h, cudaStreamSynchronize(st));
@@ -519,15 +545,15 @@ jkcals_status create_impl(jkcals_ctx* h, const void* T, int T_dtype, const int32
       h->Tn64[n] = nullptr;
       JK_TRY(dalloc_t(h, &h->UT[n], (size_t)h->C * h->Ipad[n]));
       JK_CUDA(h, cudaMemsetAsync(h->UT[n], 0, sizeof(float) * h->C * h->Ipad[n], st));
+      JK_TRY(dalloc_t(h, &h->cmax[n], (size_t)h->C));
+      if (h->opt.precision == JKCALS_EXACT_BF16) {
+        JK_TRY(dalloc_t(h, &h->UTlo[n], (size_t)h->C * h->Ipad[n]));
+        JK_CUDA(h, cudaMemsetAsync(h->UTlo[n], 0, sizeof(float) * h->C * h->Ipad[n], st));
+      }
     }
     JK_TRY(encode_tensor_maps(h));
     size_t smem = 0;
-    for (int n = 0; n < N; ++n) {
-      const TcModePlan& p = h->tcplan[n];
-      tc::TcPlan tp{p.BN, p.tiles_c, p.tiles_n, p.splits, p.stages, p.tmem_cols, p.nsplit, p.a_mode, p.Ia_pad,
-                    p.Jp, p.kchunk};
-      smem = std::max(smem, tc::tc_smem_bytes(tp));
-    }
+    for (int n = 0; n < N; ++n) smem = std::max(smem, tc::tc_smem_bytes(h->tcplan[n]));
     JK_CUDA(h, tc::prepare_mttkrp_tc(h->opt.precision, smem));
     JK_TRY(dalloc_t(h, &h->d_err, 1));
     JK_CUDA(h, cudaMemsetAsync(h->d_err, 0, sizeof(int), st));
@@ -546,8 +572,8 @@ jkcals_status create_impl(jkcals_ctx* h, const void* T, int T_dtype, const int32
   make_plan(h);
   size_t part_bytes = 0, chunks = 0;
   for (int n = 0; n < N; ++n) {
-    const size_t pb = h->tc ? (size_t)h->tcplan[n].splits * h->dims[n] * h->C * sizeof(float)
-                            : (size_t)h->plan[n].splits * h->dims[n] * h->C * sizeof(double);
+    const size_t eb = part_kind(h) == kPartF32 ? sizeof(float) : sizeof(double);
+    const size_t pb = (size_t)mode_splits(h, n) * h->dims[n] * h->C * eb;
     part_bytes = std::max(part_bytes, pb);
     chunks = std::max(chunks, (size_t)h->plan[n].upd.RC * K);
   }
@@ -585,6 +611,11 @@ jkcals_status grad_impl(jkcals_ctx* h, const double* const* U, double* const* G,
       for (int n = 0; n < N; ++n) {
         JK_TRY(dalloc_t(h, &h->gUT[n], (size_t)h->C * h->Ipad[n]));
         JK_CUDA(h, cudaMemsetAsync(h->gUT[n], 0, sizeof(float) * h->C * h->Ipad[n], st));
+        JK_TRY(dalloc_t(h, &h->gcmax[n], (size_t)h->C));
+        if (h->opt.precision == JKCALS_EXACT_BF16) {
+          JK_TRY(dalloc_t(h, &h->gUTlo[n], (size_t)h->C * h->Ipad[n]));
+          JK_CUDA(h, cudaMemsetAsync(h->gUTlo[n], 0, sizeof(float) * h->C * h->Ipad[n], st));
+        }
       }
     }
     h->grad_ready = true;
@@ -597,10 +628,13 @@ jkcals_status grad_impl(jkcals_ctx* h, const double* const* U, double* const* G,
   JK_CUDA(h, launch_zero_left_out(h->gU[h->n_hat], h->C, h->K, bm, st));
   for (int n = 0; n < N; ++n) {
     JK_CUDA(h, launch_grams(h->gU[n], h->dims[n], h->C, h->K, bm, h->ggram[n], st));
-    if (h->tc) JK_CUDA(h, tc::launch_factor_to_ut(h->gU[n], h->dims[n], h->C, h->gUT[n], h->Ipad[n], st));
+    if (h->tc) {
+      JK_CUDA(h, tc::launch_factor_to_ut(h->gU[n], h->dims[n], h->C, h->gUT[n], h->gUTlo[n], h->Ipad[n], st));
+      JK_CUDA(h, tc::launch_colmax(h->gUT[n], h->dims[n], h->Ipad[n], h->C, h->gcmax[n], st));
+    }
   }
   for (int n = 0; n < N; ++n) {
-    JK_TRY(enqueue_mttkrp(h, n, h->gU, h->gUT));
+    JK_TRY(enqueue_mttkrp(h, n, h->gU, h->gUT, h->gUTlo, h->gcmax));
     const int64_t cnt = h->dims[n] * (int64_t)h->C;
     JK_TRY(reduce_into(h, n, h->mbuf));
     if (G != nullptr && G[n] != nullptr) {
@@ -686,7 +720,7 @@ jkcals_status jkcals_create(jkcals_t* out, int N, const int64_t* dims, const voi
   jkcals_options o;
   jkcals_default_options(&o);
   if (opt) o = *opt;
-  if (o.precision < JKCALS_FP64 || o.precision > JKCALS_SPLIT_BF16) return fail(JKCALS_ERR_ARG, "bad precision");
+  if (o.precision < JKCALS_FP64 || o.precision > JKCALS_EXACT_BF16) return fail(JKCALS_ERR_ARG, "bad precision");
   if (o.splits < 0) return fail(JKCALS_ERR_ARG, "splits must be >= 0");
 
   jkcals_ctx* h = new jkcals_ctx();
@@ -731,7 +765,7 @@ jkcals_status jkcals_mttkrp(jkcals_t h, int mode, double* M_out) {
   JK_TRY(check_handle(h));
   if (mode < 0 || mode >= h->N) return fail(JKCALS_ERR_ARG, "mode out of range");
   if (M_out == nullptr) return fail(JKCALS_ERR_ARG, "M_out is NULL");
-  JK_TRY(enqueue_mttkrp(h, mode, h->U, h->UT));
+  JK_TRY(enqueue_mttkrp(h, mode, h->U, h->UT, h->UTlo, h->cmax));
   const int64_t cnt = h->dims[mode] * (int64_t)h->C;
   JK_TRY(reduce_into(h, mode, h->mbuf));
   JK_TRY(copy_out(h, M_out, h->mbuf, sizeof(double) * cnt));

@@ -55,11 +55,24 @@ struct ModePlan {
   UpdatePlan upd;
 };
 
+namespace tc {
 // Tensor-core form of one mode (see jk_tc.cuh).
-struct TcModePlan {
-  int BN, tiles_c, tiles_n, splits, stages, tmem_cols, nsplit, a_mode, Ia_pad;
-  int64_t Jp, kchunk;
+struct TcPlan {
+  int BN;          // N tile (rows of T_(n)), multiple of 16, <= 256
+  int tiles_c;     // ceil(C / 128)
+  int tiles_n;     // ceil(I_n / BN)
+  int splits;      // split-K factor
+  int stages;      // pipeline depth
+  int tmem_cols;   // power of two >= accumulators * acc_cols
+  int acc_cols;    // TMEM column stride between accumulators
+  int nsplit;      // operand parts of the form
+  int row_bytes;   // bytes of K per operand row and stage (128 or 64)
+  int a_mode;      // fastest other mode
+  int Ia_pad;      // its padded size
+  int64_t Jp;      // padded columns of the unfolding
+  int64_t kchunk;  // padded columns per split (multiple of the k-step)
 };
+}  // namespace tc
 
 }  // namespace jk
 
@@ -125,12 +138,17 @@ struct jkcals_ctx {
 
   // tensor-core forms (precision != JKCALS_FP64)
   bool tc = false;
-  void* Tp[jk::kMaxModes][3] = {{nullptr}};  // split, padded unfoldings
+  void* Tp[jk::kMaxModes][4] = {{nullptr}};  // split, padded unfoldings
   float* UT[jk::kMaxModes] = {nullptr};      // C x Ipad FP32 transposed factors
   float* gUT[jk::kMaxModes] = {nullptr};     // same, for the gradient's factor set
+  float* UTlo[jk::kMaxModes] = {nullptr};    // exact-chain form: low parts, U = UT + UTlo
+  float* gUTlo[jk::kMaxModes] = {nullptr};
   int64_t Ipad[jk::kMaxModes] = {0};
-  CUtensorMap tmap[jk::kMaxModes][3];
-  jk::TcModePlan tcplan[jk::kMaxModes];
+  CUtensorMap tmap[jk::kMaxModes][4];
+  jk::tc::TcPlan tcplan[jk::kMaxModes];
+  float* cmax[jk::kMaxModes] = {nullptr};    // column maxima of UT (exact-chain grid)
+  float* gcmax[jk::kMaxModes] = {nullptr};
+  int* rowexp[jk::kMaxModes] = {nullptr};    // row exponents of T_(n) (exact-chain grid)
   int* d_err = nullptr;                      // bounded-wait expiry code of the TC kernel
 
   cudaGraphExec_t sweep_exec = nullptr;
@@ -174,6 +192,11 @@ cudaError_t launch_reduce_partials_f64(const double* part, int S, int64_t count,
 cudaError_t launch_reduce_partials_f32(const float* part, int S, int64_t count, double* out,
                                        cudaStream_t s);
 
+// Storage of split-K partials: FP64, FP32, or an unevaluated FP32 pair (hi, lo).
+constexpr int kPartF64 = 0, kPartF32 = 1, kPartF32x2 = 2;
+cudaError_t launch_reduce_partials_f32x2(const float2* part, int S, int64_t count, double* out,
+                                         cudaStream_t s);
+
 // ---- per-block update (jk_update.cu) ----------------------------------------
 struct UpdateArgs {
   int N, n, n_hat, K, C;
@@ -183,7 +206,7 @@ struct UpdateArgs {
   const double* gram[kMaxModes];    // Grams of every mode (gram[n] written in phase B)
   double* gram_n;
   const void* part;                 // S x I x C partial MTTKRPs
-  int part_is_f32;
+  int part_kind;                    // kPartF64 / kPartF32 / kPartF32x2
   int S;
   int rows_per_chunk, RC;
   double* gpart;
@@ -199,6 +222,8 @@ struct UpdateArgs {
   const int* sweep_idx;             // device scalar
   float* UT;                        // NULL or C x I_pad FP32 transposed copy of Ubar^(n), refreshed
   int64_t I_pad;
+  float* cmax;                      // NULL or C column maxima of UT, refreshed
+  float* UT_lo;                     // NULL or the low parts fl32(U - UT), refreshed
 };
 cudaError_t launch_update(const UpdateArgs& a, cudaStream_t s);
 cudaError_t launch_advance_sweep(int* sweep_idx, cudaStream_t s);

@@ -127,7 +127,29 @@ __global__ void reduce_partials_f32_kernel(const float* __restrict__ part, int S
   }
 }
 
+__global__ void reduce_partials_f32x2_kernel(const float2* __restrict__ part, int S, int64_t count,
+                                             double* __restrict__ out) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < count;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (int s = 0; s < S; ++s) {
+      const float2 v = part[(int64_t)s * count + e];
+      acc += (double)v.x + (double)v.y;
+    }
+    out[e] = acc;
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_reduce_partials_f32x2(const float2* part, int S, int64_t count, double* out,
+                                         cudaStream_t s) {
+  int64_t blocks = (count + 255) / 256;
+  if (blocks > 4096) blocks = 4096;
+  if (blocks < 1) blocks = 1;
+  reduce_partials_f32x2_kernel<<<(unsigned)blocks, 256, 0, s>>>(part, S, count, out);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_reduce_partials_f32(const float* part, int S, int64_t count, double* out,
                                        cudaStream_t s) {

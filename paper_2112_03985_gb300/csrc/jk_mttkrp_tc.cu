@@ -9,196 +9,57 @@
 // tile), while the long contraction over J is split across CTAs (split-K).
 //
 // Roles inside one CTA (6 warps, one CTA per SM):
-//   warp 0     TMA producer: streams BN x 128-byte tiles of the (pre-split)
-//              unfolding T_(n) into shared memory (128B swizzle, K-major).
-//   warp 1     owns TMEM; one lane issues tcgen05.mma (kind::tf32 or
+//   warp 0     TMA producer: streams BN-row tiles of the (pre-split) unfolding
+//              T_(n) into shared memory (K-major, 128- or 64-byte swizzle).
+//   warp 1     owns TMEM; one lane issues tcgen05.mma (kind::tf32, or
 //              kind::f16 with BF16 operands) for every (A-part, B-part) pair
 //              of the precision form, accumulating in FP32 in TMEM.
 //   warps 2-5  build the 128 x BK tile of KRP_n^T in shared memory straight
-//              into the UMMA K-major 128B-swizzled layout: element (c, j) =
-//              U_a^T(c, i_a(j)) * prod_{other k} U_k^T(c, i_k(j)), computed in
-//              FP32 from transposed FP32 copies of the factor multi-matrices,
-//              then split into TF32 hi/lo or BF16 hi/mid/lo parts.  After the
-//              main loop they drain TMEM (tcgen05.ld 32x32b) and write the
-//              FP32 partial tile of Mbar_n for this split.
+//              into the UMMA K-major swizzled layout: element (c, j) =
+//              U_a^T(c, i_a(j)) * prod_{other k} U_k^T(c, i_k(j)), in FP32 from
+//              transposed FP32 copies of the factor multi-matrices, then split
+//              into the form's parts.  After the main loop they drain TMEM
+//              (tcgen05.ld 32x32b) and write this split's FP32 partial of Mbar_n.
 // The Khatri-Rao product never exists in global memory.
+//
+// Exact-chain form (JKCALS_EXACT_BF16): every operand value x of a row whose
+// magnitudes stay below 2^E is written as x = 2^(E-7) (s0 + s1/2^7 + s2/2^14 +
+// s3/2^21) with integers |s_k| <= 128 (round-to-nearest extraction, exact in
+// FP32) and stored as BF16 s_k * 2^(-7k).  Products of level 0 (s0 t0) and of
+// level 1 (s0 t1 + s1 t0) are integer multiples of 1 and 2^-7 whose chain sums
+// stay below 2^24 units for chains of <= 1024 columns, so they accumulate
+// exactly in FP32 TMEM; levels 2-3 share a third accumulator whose truncation
+// is scaled by 2^-14.  The epilogue adds the three in FP64 and applies
+// 2^(E_c - 7) 2^(F_i - 7).
 //
 // Synchronisation: mbarriers per stage (T tile landed / KRP tile written /
 // stage consumed) plus one for the accumulator.  Every wait is bounded by a
 // wall-clock limit; on expiry the CTA records an error code, stops, waits
-// (bounded) for its own TMA copies, frees its TMEM and returns.
+// (bounded) for its own TMA copies and MMAs, frees its TMEM and returns.
 #include <cuda.h>
-#include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 
 #include "jk_common.cuh"
+#include "jk_ptx.cuh"
 #include "jk_tc.cuh"
 
 namespace jk {
 namespace tc {
 namespace {
 
+using namespace ptx;
+
 constexpr int kThreads = 192;
 constexpr int kProducerWarp0 = 2;
-constexpr int kRowsM = 128;                       // MMA M
-constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s per wait
+constexpr int kRowsM = 128;   // MMA M
 
-// ---- small PTX wrappers ------------------------------------------------------
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-               : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-__device__ __forceinline__ uint64_t global_ns() {
-  uint64_t t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
-// Bounded wait for the phase with the given parity.  Returns false if this
-// CTA aborted (another role timed out) or the limit expired (then it aborts).
-__device__ __forceinline__ bool wait_bounded(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
-                                             int* err, int code) {
-  if (mbar_try_wait(bar, parity)) return true;
-  const uint64_t t0 = global_ns();
-  while (true) {
-    if (mbar_try_wait(bar, parity)) return true;
-    if (*abort_flag) return false;
-    if (global_ns() - t0 > kWaitLimitNs) {
-      *abort_flag = 1;
-      atomicExch(err, code);
-      return false;
-    }
-  }
-}
-
-// Bounded wait that ignores the abort flag (used to drain own TMA copies).
-__device__ __forceinline__ void wait_drain(uint64_t* bar, uint32_t parity) {
-  const uint64_t t0 = global_ns();
-  while (!mbar_try_wait(bar, parity)) {
-    if (global_ns() - t0 > kWaitLimitNs) return;
-  }
-}
-
-__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
-          smem_u32(dst)),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y)
-      : "memory");
-}
-
-__device__ __forceinline__ void tma_prefetch_desc(const CUtensorMap* map) {
-  asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
-}
-
-__device__ __forceinline__ void fence_async_shared() {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-
-__device__ __forceinline__ void fence_barrier_init() {
-  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-
-__device__ __forceinline__ void tc_fence_before() {
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-}
-
-__device__ __forceinline__ void tc_fence_after() {
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-}
-
-__device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t ncols) {
-  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)),
-               "r"(ncols)
-               : "memory");
-  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-}
-
-__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
-  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
-}
-
-__device__ __forceinline__ void tc_commit(uint64_t* bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
-               : "memory");
-}
-
-template <int KIND>
-__device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
-                                       uint32_t accumulate) {
-  if constexpr (KIND == kKindTF32) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-        "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
-        : "memory");
-  } else {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-        "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
-        : "memory");
-  }
-}
-
-// 32 lanes x 32 consecutive 32-bit TMEM columns -> 32 registers per thread.
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
-      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
-      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-        "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
-        "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]),
-        "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]),
-        "=r"(v[30]), "=r"(v[31])
-      : "r"(taddr));
-}
-
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[32]) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
-      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
-      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-        "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
-      : "r"(taddr));
-}
-
-__device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
-
-// UMMA shared-memory descriptor: K-major operand, 128-byte swizzle, 8-row
-// groups 1024 bytes apart (SBO), version 1 (tcgen05).
-__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
-  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
-         ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+// UMMA shared-memory descriptor: K-major operand, ROW-byte swizzle (128 -> 2,
+// 64 -> 4), 8-row groups 8*ROW bytes apart (SBO), version 1 (tcgen05).
+template <int ROW>
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
+  constexpr uint64_t layout = ROW == 128 ? 2 : 4;
+  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)((8 * ROW) >> 4) << 32) |
+         ((uint64_t)1 << 46) | (layout << 61);
 }
 
 // Instruction descriptor: FP32 accumulator, A/B format fmt (TF32 = 2 under
@@ -213,10 +74,40 @@ __device__ __forceinline__ float tf32_rna(float x) {
   return __uint_as_float(r);
 }
 
-// Split one FP32 value into NS parts (Cfg::kind) and return their bit patterns.
+// 2^k as FP32 for k in [-126, 127]
+__device__ __forceinline__ float pow2f(int k) { return __int_as_float((127 + k) << 23); }
+
+// Smallest E (clamped to [-110, 110]) with |values| < 2^E given a bound b >= 0.
+__device__ __forceinline__ int bound_exponent(double b) {
+  if (!(b > 0.0)) return 0;
+  int e;
+  frexp(b, &e);   // b = m 2^e, m in [0.5, 1)
+  return e < -110 ? -110 : (e > 110 ? 110 : e);
+}
+
+// Split one FP32 value into the form's parts (returned as FP32 values that the
+// part's storage type represents exactly).
 template <class Cfg>
-__device__ __forceinline__ void split_value(float v, float (&p)[3]) {
-  if constexpr (Cfg::kind == kKindTF32) {
+__device__ __forceinline__ void split_value(float v, float vl, float scale, float (&p)[4]) {
+  if constexpr (Cfg::exact) {
+    // y = (v + vl) * scale lies in [-128, 128].  (r + M_k) - M_k with M_k =
+    // 1.5 * 2^(23 - 7k) rounds r to the nearest multiple of 2^(-7k) (FP32
+    // round-to-nearest), so each slice comes out already scaled by 2^(-7k);
+    // every step is exact except adding the low part after the first slice
+    // (error below 2^-25 of the grid unit).
+    float y = __fmul_rn(v, scale);
+    const float s0 = __fsub_rn(__fadd_rn(y, 12582912.f), 12582912.f);          // M = 1.5 * 2^23
+    y = __fadd_rn(__fsub_rn(y, s0), __fmul_rn(vl, scale));
+    const float s1 = __fsub_rn(__fadd_rn(y, 98304.f), 98304.f);                 // M = 1.5 * 2^16
+    y = __fsub_rn(y, s1);
+    const float s2 = __fsub_rn(__fadd_rn(y, 768.f), 768.f);                     // M = 1.5 * 2^9
+    y = __fsub_rn(y, s2);
+    const float s3 = __fsub_rn(__fadd_rn(y, 6.f), 6.f);                         // M = 1.5 * 2^2
+    p[0] = s0;
+    p[1] = s1;
+    p[2] = s2;
+    p[3] = s3;
+  } else if constexpr (Cfg::kind == kKindTF32) {
     const float h = tf32_rna(v);
     p[0] = h;
     if constexpr (Cfg::nsplit > 1) p[1] = tf32_rna(v - h);
@@ -232,25 +123,24 @@ __device__ __forceinline__ void split_value(float v, float (&p)[3]) {
   }
 }
 
-// Shared-memory plan (host and device agree through TcArgs).
-struct SmemPlan {
-  uint32_t a_bytes;      // one A part: 128 rows x 128 B
-  uint32_t b_bytes;      // one B part: BN rows x 128 B
-  uint32_t stage_bytes;  // nsplit * (a + b)
-};
-
 template <class Cfg>
 __global__ void __launch_bounds__(kThreads, 1)
     mttkrp_tc_kernel(const __grid_constant__ CUtensorMap tm0, const __grid_constant__ CUtensorMap tm1,
-                     const __grid_constant__ CUtensorMap tm2, const TcArgs a) {
+                     const __grid_constant__ CUtensorMap tm2, const __grid_constant__ CUtensorMap tm3,
+                     const TcArgs a) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
-  // 1024-byte aligned base for the swizzled tiles
   unsigned char* smem =
       reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   constexpr int NS = Cfg::nsplit;
+  constexpr int ROW = Cfg::row_bytes;            // bytes of K per operand row in one stage
+  constexpr int BK = ROW / Cfg::elem;            // columns of T_(n) per stage
+  constexpr int CHUNK = 16 / Cfg::elem;          // elements per 16-byte chunk
+  constexpr int CPR = ROW / 16;                  // chunks per row
+  constexpr int RPI = 32 / CPR;                  // rows covered by one warp instruction
+  constexpr int ROWS_PER_THREAD = 32 / RPI;      // rows per producer thread per stage
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const uint32_t a_bytes = kRowsM * 128;
-  const uint32_t b_bytes = (uint32_t)a.BN * 128;
+  const uint32_t a_bytes = kRowsM * ROW;
+  const uint32_t b_bytes = (uint32_t)a.BN * ROW;
   const uint32_t stage_bytes = NS * (a_bytes + b_bytes);
   const int STAGES = a.stages;
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + (size_t)STAGES * stage_bytes);
@@ -266,7 +156,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int64_t jb = (int64_t)blockIdx.z * a.kchunk;
   int64_t je = jb + a.kchunk;
   if (je > a.Jp) je = a.Jp;
-  const int nk = (je > jb) ? (int)((je - jb + Cfg::bk - 1) / Cfg::bk) : 0;
+  const int nk = (je > jb) ? (int)((je - jb + BK - 1) / BK) : 0;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -280,6 +170,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     tma_prefetch_desc(&tm0);
     if (NS > 1) tma_prefetch_desc(&tm1);
     if (NS > 2) tma_prefetch_desc(&tm2);
+    if (NS > 3) tma_prefetch_desc(&tm3);
   }
   if (warp == 1) tmem_alloc(tmem_slot, (uint32_t)a.tmem_cols);
   tc_fence_before();
@@ -301,10 +192,11 @@ __global__ void __launch_bounds__(kThreads, 1)
         const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
         if (!wait_bounded(&empty[s], ph ^ 1u, abort_flag, a.err, 1)) break;
         mbar_arrive_expect_tx(&full_b[s], NS * b_bytes);
-        const int x = (int)(jb + (int64_t)it * Cfg::bk);
+        const int x = (int)(jb + (int64_t)it * BK);
         tma_load_2d(b_tile(s, 0), &tm0, &full_b[s], x, n0);
         if (NS > 1) tma_load_2d(b_tile(s, 1), &tm1, &full_b[s], x, n0);
         if (NS > 2) tma_load_2d(b_tile(s, 2), &tm2, &full_b[s], x, n0);
+        if (NS > 3) tma_load_2d(b_tile(s, 3), &tm3, &full_b[s], x, n0);
         issued = it + 1;
       }
       if (*abort_flag) {
@@ -326,12 +218,14 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (!ok) break;
         tc_fence_after();
 #pragma unroll
-        for (int kk = 0; kk < 4; ++kk) {
+        for (int kk = 0; kk < ROW / 32; ++kk) {
 #pragma unroll
           for (int q = 0; q < Cfg::npass; ++q) {
-            const uint64_t ad = sw128_desc(smem_u32(a_tile(s, Cfg::pass_a(q))) + kk * 32);
-            const uint64_t bd = sw128_desc(smem_u32(b_tile(s, Cfg::pass_b(q))) + kk * 32);
-            tc_mma<Cfg::kind>(tmem, ad, bd, idesc, (it > 0 || kk > 0 || q > 0) ? 1u : 0u);
+            const uint64_t ad = smem_desc<ROW>(smem_u32(a_tile(s, Cfg::pass_a(q))) + kk * 32);
+            const uint64_t bd = smem_desc<ROW>(smem_u32(b_tile(s, Cfg::pass_b(q))) + kk * 32);
+            const uint32_t d = tmem + (uint32_t)(Cfg::pass_acc(q) * a.acc_cols);
+            const bool first = (it == 0 && kk == 0 && Cfg::first_of_acc(q));
+            tc_mma<Cfg::kind>(d, ad, bd, idesc, first ? 0u : 1u);
           }
         }
         tc_commit(&empty[s]);
@@ -344,8 +238,24 @@ __global__ void __launch_bounds__(kThreads, 1)
   } else {
     // ---------------- Khatri-Rao producers (warps 2..5) ------------------------------
     const int pw = warp - kProducerWarp0;   // 0..3
-    const int r4 = lane >> 3;               // row within a group of 4
-    const int q = lane & 7;                 // 16-byte chunk within the 128-byte row
+    const int rg = lane / CPR;              // row within a group of RPI rows
+    const int q = lane % CPR;               // 16-byte chunk within the row
+    // per-row scale of the exact-chain form: 2^(7 - E_c)
+    float rscale[ROWS_PER_THREAD];
+#pragma unroll
+    for (int rr = 0; rr < ROWS_PER_THREAD; ++rr) {
+      rscale[rr] = 1.f;
+      if constexpr (Cfg::exact) {
+        const int c = c0 + pw * 32 + rr * RPI + rg;
+        if (c < a.C) {
+          double b = (double)__ldg(a.cmax_a + c);
+#pragma unroll
+          for (int t = 0; t < kMaxModes - 2; ++t)
+            if (t < a.nq) b *= (double)__ldg(a.cmax_q[t] + c);
+          rscale[rr] = pow2f(7 - bound_exponent(b));
+        }
+      }
+    }
     bool ok = true;
     for (int it = 0; it < nk && ok; ++it) {
       const int s = it % STAGES;
@@ -354,7 +264,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         ok = false;
         break;
       }
-      const int64_t j = jb + (int64_t)it * Cfg::bk + q * Cfg::chunk;
+      const int64_t j = jb + (int64_t)it * BK + q * CHUNK;
       const bool jvalid = j < je;
       int ia = 0;
       int iq[kMaxModes - 2];
@@ -372,36 +282,66 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
       }
 #pragma unroll 2
-      for (int rr = 0; rr < 8; ++rr) {
-        const int m = pw * 32 + rr * 4 + r4;   // row of the A tile = column c0 + m
+      for (int rr = 0; rr < ROWS_PER_THREAD; ++rr) {
+        const int m = pw * 32 + rr * RPI + rg;   // row of the A tile = column c0 + m
         const int c = c0 + m;
-        float v[Cfg::chunk];
+        float v[CHUNK], vl[CHUNK];
 #pragma unroll
-        for (int e = 0; e < Cfg::chunk; ++e) v[e] = 0.f;
+        for (int e = 0; e < CHUNK; ++e) v[e] = vl[e] = 0.f;
         if (jvalid && c < a.C) {
-          float qv = 1.f;
+          if constexpr (!Cfg::exact) {
+            float qv = 1.f;
 #pragma unroll
-          for (int t = 0; t < kMaxModes - 2; ++t)
-            if (t < a.nq) qv *= __ldg(a.UTq[t] + (int64_t)c * a.qpad[t] + iq[t]);
-          const float4* src = reinterpret_cast<const float4*>(a.UTa + (int64_t)c * a.Ia_pad + ia);
+            for (int t = 0; t < kMaxModes - 2; ++t)
+              if (t < a.nq) qv *= __ldg(a.UTq[t] + (int64_t)c * a.qpad[t] + iq[t]);
+            const float4* src = reinterpret_cast<const float4*>(a.UTa + (int64_t)c * a.Ia_pad + ia);
 #pragma unroll
-          for (int e4 = 0; e4 < Cfg::chunk / 4; ++e4) {
-            const float4 u = __ldg(src + e4);
-            v[4 * e4 + 0] = u.x * qv;
-            v[4 * e4 + 1] = u.y * qv;
-            v[4 * e4 + 2] = u.z * qv;
-            v[4 * e4 + 3] = u.w * qv;
+            for (int e4 = 0; e4 < CHUNK / 4; ++e4) {
+              const float4 u = __ldg(src + e4);
+              v[4 * e4 + 0] = u.x * qv;
+              v[4 * e4 + 1] = u.y * qv;
+              v[4 * e4 + 2] = u.z * qv;
+              v[4 * e4 + 3] = u.w * qv;
+            }
+          } else {
+            // Khatri-Rao entry as an unevaluated pair (v + vl) from hi/lo factor
+            // copies: error-free products (FMA) keep it to ~2^-44 relative
+            float qh = 1.f, ql = 0.f;
+#pragma unroll
+            for (int t = 0; t < kMaxModes - 2; ++t) {
+              if (t < a.nq) {
+                const int64_t idx = (int64_t)c * a.qpad[t] + iq[t];
+                const float bh = __ldg(a.UTq[t] + idx), bl = __ldg(a.UTq_lo[t] + idx);
+                const float pq = __fmul_rn(qh, bh);
+                const float eq = __fadd_rn(__fmaf_rn(qh, bh, -pq), __fmaf_rn(qh, bl, __fmul_rn(ql, bh)));
+                qh = pq;
+                ql = eq;
+              }
+            }
+            const float4* src = reinterpret_cast<const float4*>(a.UTa + (int64_t)c * a.Ia_pad + ia);
+            const float4* srcl = reinterpret_cast<const float4*>(a.UTa_lo + (int64_t)c * a.Ia_pad + ia);
+#pragma unroll
+            for (int e4 = 0; e4 < CHUNK / 4; ++e4) {
+              const float4 u = __ldg(src + e4), ul = __ldg(srcl + e4);
+              const float uh4[4] = {u.x, u.y, u.z, u.w}, ul4[4] = {ul.x, ul.y, ul.z, ul.w};
+#pragma unroll
+              for (int k = 0; k < 4; ++k) {
+                const float p = __fmul_rn(uh4[k], qh);
+                v[4 * e4 + k] = p;
+                vl[4 * e4 + k] = __fadd_rn(__fmaf_rn(uh4[k], qh, -p), __fmaf_rn(uh4[k], ql, __fmul_rn(ul4[k], qh)));
+              }
+            }
           }
         }
-        // split and store the 16-byte chunk of every part (128B swizzle)
-        const uint32_t off = (uint32_t)(m >> 3) * 1024u + (uint32_t)(m & 7) * 128u + (uint32_t)((q ^ (m & 7)) << 4);
-        float parts[NS][Cfg::chunk];
+        const int sw = (ROW == 128) ? (m & 7) : ((m >> 1) & 3);
+        const uint32_t off = (uint32_t)(m >> 3) * (8u * ROW) + (uint32_t)(m & 7) * ROW + (uint32_t)((q ^ sw) << 4);
+        float parts[NS][CHUNK];
 #pragma unroll
-        for (int e = 0; e < Cfg::chunk; ++e) {
-          float p3[3];
-          split_value<Cfg>(v[e], p3);
+        for (int e = 0; e < CHUNK; ++e) {
+          float p4[4];
+          split_value<Cfg>(v[e], vl[e], rscale[rr], p4);
 #pragma unroll
-          for (int p = 0; p < NS; ++p) parts[p][e] = p3[p];
+          for (int p = 0; p < NS; ++p) parts[p][e] = p4[p];
         }
 #pragma unroll
         for (int p = 0; p < NS; ++p) {
@@ -435,22 +375,74 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int quarter = warp & 3;             // TMEM lanes 32*quarter .. +31
     const int m = quarter * 32 + lane;
     const int c = c0 + m;
-    float* out = a.part + (int64_t)blockIdx.z * a.I * a.C;
-    for (int cc = 0; cc < a.BN; cc += 32) {
-      uint32_t v[32];
-      const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)cc;
-      const int width = (a.BN - cc >= 32) ? 32 : 16;
-      if (have) {
-        if (width == 32)
-          tmem_ld32(taddr, v);
-        else
-          tmem_ld16(taddr, v);
-        tmem_ld_wait();
-      }
+    int Ec = 0;
+    if constexpr (Cfg::exact) {
+      if (c < a.C) {
+        double b = (double)__ldg(a.cmax_a + c);
 #pragma unroll
-      for (int r = 0; r < 32; ++r) {
-        const int64_t i = (int64_t)n0 + cc + r;
-        if (r < width && i < a.I && c < a.C) out[i * a.C + c] = have ? __uint_as_float(v[r]) : 0.f;
+        for (int t = 0; t < kMaxModes - 2; ++t)
+          if (t < a.nq) b *= (double)__ldg(a.cmax_q[t] + c);
+        Ec = bound_exponent(b);
+      }
+    }
+    float* out = a.part + (int64_t)blockIdx.z * a.I * a.C;
+    const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16);
+    for (int cc = 0; cc < a.BN; cc += 32) {
+      const int width = (a.BN - cc >= 32) ? 32 : 16;
+      uint32_t v[32];
+      if constexpr (!Cfg::exact) {
+        if (have) {
+          if (width == 32)
+            tmem_ld32(lane_base + (uint32_t)cc, v);
+          else
+            tmem_ld16(lane_base + (uint32_t)cc, v);
+          tmem_ld_wait();
+        }
+#pragma unroll
+        for (int r = 0; r < 32; ++r) {
+          const int64_t i = (int64_t)n0 + cc + r;
+          if (r < width && i < a.I && c < a.C) out[i * a.C + c] = have ? __uint_as_float(v[r]) : 0.f;
+        }
+      } else {
+        uint32_t v1[32], v2[32];
+        if (have) {
+          if (width == 32) {
+            tmem_ld32(lane_base + (uint32_t)cc, v);
+            tmem_ld32(lane_base + (uint32_t)(a.acc_cols + cc), v1);
+            tmem_ld32(lane_base + (uint32_t)(2 * a.acc_cols + cc), v2);
+          } else {
+            tmem_ld16(lane_base + (uint32_t)cc, v);
+            tmem_ld16(lane_base + (uint32_t)(a.acc_cols + cc), v1);
+            tmem_ld16(lane_base + (uint32_t)(2 * a.acc_cols + cc), v2);
+          }
+          tmem_ld_wait();
+        }
+        // level 0 and level 1 are exact; add the three as an unevaluated FP32 pair
+        // (hi, lo) with error-free TwoSum steps, scale by 2^(E_c + F_i - 14) and
+        // store the pair; the consumer adds hi + lo in FP64
+        float2* out2 = reinterpret_cast<float2*>(a.part) + (int64_t)blockIdx.z * a.I * a.C;
+#pragma unroll
+        for (int r = 0; r < 32; ++r) {
+          const int64_t i = (int64_t)n0 + cc + r;
+          if (r < width && i < a.I && c < a.C) {
+            float2 val = make_float2(0.f, 0.f);
+            if (have) {
+              const float l0 = __uint_as_float(v[r]), l1 = __uint_as_float(v1[r]), l2 = __uint_as_float(v2[r]);
+              const float s = __fadd_rn(l0, l1);
+              const float bb = __fsub_rn(s, l0);
+              const float e1 = __fadd_rn(__fsub_rn(l0, __fsub_rn(s, bb)), __fsub_rn(l1, bb));
+              const float t = __fadd_rn(s, l2);
+              const float b2 = __fsub_rn(t, s);
+              const float e2 = __fadd_rn(__fsub_rn(s, __fsub_rn(t, b2)), __fsub_rn(l2, b2));
+              float lo = __fadd_rn(e1, e2);
+              const float hi = __fadd_rn(t, lo);
+              lo = __fsub_rn(lo, __fsub_rn(hi, t));
+              const int k = Ec + __ldg(a.rowexp + i) - 2 * kSliceBits;
+              val = make_float2(ldexpf(hi, k), ldexpf(lo, k));
+            }
+            out2[i * a.C + c] = val;
+          }
+        }
       }
     }
   }
@@ -466,26 +458,51 @@ __global__ void __launch_bounds__(kThreads, 1)
 // ---- precision forms -----------------------------------------------------------
 
 struct CfgTF32 {
-  static constexpr int kind = kKindTF32, fmt = 2, nsplit = 1, npass = 1, bk = 32, chunk = 4;
+  static constexpr int kind = kKindTF32, fmt = 2, nsplit = 1, npass = 1, row_bytes = 128, elem = 4;
+  static constexpr bool exact = false;
   __device__ static constexpr int pass_a(int) { return 0; }
   __device__ static constexpr int pass_b(int) { return 0; }
+  __device__ static constexpr int pass_acc(int) { return 0; }
+  __device__ static constexpr bool first_of_acc(int q) { return q == 0; }
 };
 struct Cfg3xTF32 {
   // hi*hi + hi*lo + lo*hi
-  static constexpr int kind = kKindTF32, fmt = 2, nsplit = 2, npass = 3, bk = 32, chunk = 4;
+  static constexpr int kind = kKindTF32, fmt = 2, nsplit = 2, npass = 3, row_bytes = 128, elem = 4;
+  static constexpr bool exact = false;
   __device__ static constexpr int pass_a(int q) { return q == 2 ? 1 : 0; }
   __device__ static constexpr int pass_b(int q) { return q == 1 ? 1 : 0; }
+  __device__ static constexpr int pass_acc(int) { return 0; }
+  __device__ static constexpr bool first_of_acc(int q) { return q == 0; }
 };
 struct CfgBF16 {
-  static constexpr int kind = kKindBF16, fmt = 1, nsplit = 1, npass = 1, bk = 64, chunk = 8;
+  static constexpr int kind = kKindBF16, fmt = 1, nsplit = 1, npass = 1, row_bytes = 128, elem = 2;
+  static constexpr bool exact = false;
   __device__ static constexpr int pass_a(int) { return 0; }
   __device__ static constexpr int pass_b(int) { return 0; }
+  __device__ static constexpr int pass_acc(int) { return 0; }
+  __device__ static constexpr bool first_of_acc(int q) { return q == 0; }
 };
 struct CfgBF16x3 {
   // (a, b) part pairs with a + b <= 2: hh, hm, mh, hl, lh, mm
-  static constexpr int kind = kKindBF16, fmt = 1, nsplit = 3, npass = 6, bk = 64, chunk = 8;
+  static constexpr int kind = kKindBF16, fmt = 1, nsplit = 3, npass = 6, row_bytes = 128, elem = 2;
+  static constexpr bool exact = false;
   __device__ static constexpr int pass_a(int q) { return q == 2 ? 1 : q == 4 ? 2 : q == 5 ? 1 : 0; }
   __device__ static constexpr int pass_b(int q) { return q == 1 ? 1 : q == 3 ? 2 : q == 5 ? 1 : 0; }
+  __device__ static constexpr int pass_acc(int) { return 0; }
+  __device__ static constexpr bool first_of_acc(int q) { return q == 0; }
+};
+struct CfgExact {
+  // slice pairs (s, t) with s + t <= 3; accumulators: level 0 | level 1 | levels 2-3
+  static constexpr int kind = kKindBF16, fmt = 1, nsplit = 4, npass = 10, row_bytes = 64, elem = 2;
+  static constexpr bool exact = true;
+  __device__ static constexpr int pass_a(int q) {
+    return q == 2 ? 1 : q == 4 ? 1 : q == 5 ? 2 : q == 7 ? 1 : q == 8 ? 2 : q == 9 ? 3 : 0;
+  }
+  __device__ static constexpr int pass_b(int q) {
+    return q == 1 ? 1 : q == 3 ? 2 : q == 4 ? 1 : q == 6 ? 3 : q == 7 ? 2 : q == 8 ? 1 : 0;
+  }
+  __device__ static constexpr int pass_acc(int q) { return q == 0 ? 0 : (q <= 2 ? 1 : 2); }
+  __device__ static constexpr bool first_of_acc(int q) { return q == 0 || q == 1 || q == 3; }
 };
 
 template <class Cfg>
@@ -497,7 +514,7 @@ template <class Cfg>
 cudaError_t launch_cfg(const TcPlan& p, const CUtensorMap* maps, const TcArgs& a, cudaStream_t s) {
   const size_t smem = tc_smem_bytes(p);
   dim3 grid((unsigned)p.tiles_c, (unsigned)p.tiles_n, (unsigned)p.splits);
-  mttkrp_tc_kernel<Cfg><<<grid, kThreads, smem, s>>>(maps[0], maps[1], maps[2], a);
+  mttkrp_tc_kernel<Cfg><<<grid, kThreads, smem, s>>>(maps[0], maps[1], maps[2], maps[3], a);
   return cudaGetLastError();
 }
 
@@ -509,25 +526,29 @@ int form_nsplit(int precision) {
     case JKCALS_3XTF32: return Cfg3xTF32::nsplit;
     case JKCALS_BF16: return CfgBF16::nsplit;
     case JKCALS_SPLIT_BF16: return CfgBF16x3::nsplit;
+    case JKCALS_EXACT_BF16: return CfgExact::nsplit;
     default: return 0;
   }
 }
 
-int form_bk(int precision) { return (precision == JKCALS_BF16 || precision == JKCALS_SPLIT_BF16) ? 64 : 32; }
-int form_elem_bytes(int precision) { return (precision == JKCALS_BF16 || precision == JKCALS_SPLIT_BF16) ? 2 : 4; }
-int form_chunk(int precision) { return form_bk(precision) / 8; }
+int form_row_bytes(int precision) { return precision == JKCALS_EXACT_BF16 ? 64 : 128; }
+int form_elem_bytes(int precision) { return (precision == JKCALS_TF32 || precision == JKCALS_3XTF32) ? 4 : 2; }
+int form_bk(int precision) { return form_row_bytes(precision) / form_elem_bytes(precision); }
+int form_chunk(int precision) { return 16 / form_elem_bytes(precision); }
 int form_passes(int precision) {
   switch (precision) {
     case JKCALS_TF32: return CfgTF32::npass;
     case JKCALS_3XTF32: return Cfg3xTF32::npass;
     case JKCALS_BF16: return CfgBF16::npass;
     case JKCALS_SPLIT_BF16: return CfgBF16x3::npass;
+    case JKCALS_EXACT_BF16: return CfgExact::npass;
     default: return 0;
   }
 }
 
 size_t tc_smem_bytes(const TcPlan& p) {
-  const size_t stage = (size_t)p.nsplit * (kRowsM * 128 + (size_t)p.BN * 128);
+  const size_t row = (size_t)p.row_bytes;
+  const size_t stage = (size_t)p.nsplit * (kRowsM * row + (size_t)p.BN * row);
   return 1024 /*alignment slack*/ + (size_t)p.stages * stage + (3 * p.stages + 1) * 8 + 16;
 }
 
@@ -537,6 +558,7 @@ cudaError_t prepare_mttkrp_tc(int precision, size_t max_smem) {
     case JKCALS_3XTF32: return set_smem_cfg<Cfg3xTF32>(max_smem);
     case JKCALS_BF16: return set_smem_cfg<CfgBF16>(max_smem);
     case JKCALS_SPLIT_BF16: return set_smem_cfg<CfgBF16x3>(max_smem);
+    case JKCALS_EXACT_BF16: return set_smem_cfg<CfgExact>(max_smem);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -548,6 +570,7 @@ cudaError_t launch_mttkrp_tc(int precision, const TcPlan& p, const CUtensorMap* 
     case JKCALS_3XTF32: return launch_cfg<Cfg3xTF32>(p, maps, a, s);
     case JKCALS_BF16: return launch_cfg<CfgBF16>(p, maps, a, s);
     case JKCALS_SPLIT_BF16: return launch_cfg<CfgBF16x3>(p, maps, a, s);
+    case JKCALS_EXACT_BF16: return launch_cfg<CfgExact>(p, maps, a, s);
     default: return cudaErrorInvalidValue;
   }
 }

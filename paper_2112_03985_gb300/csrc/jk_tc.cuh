@@ -1,6 +1,6 @@
-// Declarations of the tensor-core (tcgen05) form of the concurrent MTTKRP.
+// Declarations of the tensor-core (tcgen05) forms of the concurrent MTTKRP.
 //
-// Operand layouts in HBM (one handle, precision forms TF32 / 3xTF32 / BF16 / BF16x3):
+// Operand layouts in HBM (one handle, forms TF32 / 3xTF32 / BF16 / BF16x3 / exact BF16):
 //   Tp[n][p]  part p of the split mode-n unfolding, I_n x Jp_n row-major (FP32
 //             holding TF32 values, or BF16), Jp_n = Ia_pad * prod(remaining dims):
 //             the fastest other mode a is padded with zeros to Ia_pad (a multiple
@@ -8,6 +8,8 @@
 //             the remaining modes.
 //   UT[n]     FP32 transposed copy of Ubar^(n): C x I_pad_n (zero padded), written
 //             by the update kernel after every mode update.
+//   cmax[n]   C floats, max_i |UT[n][c][i]| (exact-chain form: per-row grid of KRP^T).
+//   rowexp[n] I_n ints, F_i with max_j |T_(n)(i, j)| < 2^F_i (exact-chain form).
 #pragma once
 
 #include <cuda.h>
@@ -17,26 +19,17 @@
 namespace jk {
 namespace tc {
 
-constexpr int kKindTF32 = 0;
-constexpr int kKindBF16 = 1;
+// Exact-chain sliced-BF16 form: 4 slices of 7-bit integers per operand on a
+// per-row power-of-two grid; a CTA's chain never exceeds this many columns of
+// T_(n), so that the two leading product levels sum exactly in FP32.
+constexpr int kExactChainMax = 1024;
+constexpr int kSliceBits = 7;
 
-struct TcPlan {
-  int BN;          // N tile (rows of T_(n)), multiple of 16, <= 256
-  int tiles_c;     // ceil(C / 128)
-  int tiles_n;     // ceil(I_n / BN)
-  int splits;      // split-K factor
-  int stages;      // pipeline depth
-  int tmem_cols;   // power of two >= BN
-  int nsplit;      // operand parts of the form
-  int a_mode;      // fastest other mode
-  int Ia_pad;      // its padded size
-  int64_t Jp;      // padded columns of the unfolding
-  int64_t kchunk;  // padded columns per split (multiple of the k-step)
-};
 
 struct TcArgs {
   int64_t I, Jp, kchunk;
   int C, BN, tmem_cols, stages;
+  int acc_cols;                    // TMEM column stride between accumulators
   int Ia_pad;
   int nq;                          // remaining other modes (N - 2)
   int qdims[kMaxModes - 2];
@@ -45,9 +38,16 @@ struct TcArgs {
   const float* UTq[kMaxModes - 2];  // C x qpad[t]
   float* part;                     // splits x I x C
   int* err;                        // device error word (bounded-wait expiry)
+  // exact-chain form only:
+  const float* UTa_lo;             // low parts: U = UT + UT_lo to ~2^-48
+  const float* UTq_lo[kMaxModes - 2];
+  const float* cmax_a;             // C: max_i |UT_a[c][i]|
+  const float* cmax_q[kMaxModes - 2];
+  const int* rowexp;               // I_n: F_i of this mode's unfolding
 };
 
 int form_nsplit(int precision);
+int form_row_bytes(int precision);
 int form_bk(int precision);
 int form_elem_bytes(int precision);
 int form_chunk(int precision);
@@ -59,9 +59,17 @@ cudaError_t launch_mttkrp_tc(int precision, const TcPlan& p, const CUtensorMap* 
                              cudaStream_t s);
 
 // create-time conversions (jk_tc_prep.cu)
+// rowexp[i] = smallest F with max_j |Tn64(i, j)| < 2^F (0 for an all-zero row)
+cudaError_t launch_row_exponent(const double* Tn64, int64_t I, int64_t J, int* rowexp, cudaStream_t s);
+// split (and for the exact form slice, using rowexp) the padded unfolding into its parts
 cudaError_t launch_split_unfold(int precision, const double* Tn64, int64_t I, int64_t J, int64_t Ia,
-                                int64_t Ia_pad, int64_t Jp, void* const* parts, cudaStream_t s);
-cudaError_t launch_factor_to_ut(const double* U, int64_t I, int C, float* UT, int64_t I_pad, cudaStream_t s);
+                                int64_t Ia_pad, int64_t Jp, const int* rowexp, void* const* parts,
+                                cudaStream_t s);
+// UT[c][i] = fl32(U[i][c]); if UT_lo != NULL also UT_lo[c][i] = fl32(U[i][c] - UT[c][i])
+cudaError_t launch_factor_to_ut(const double* U, int64_t I, int C, float* UT, float* UT_lo, int64_t I_pad,
+                                cudaStream_t s);
+// cmax[c] = max_{i < I} |UT[c][i]| for all C columns
+cudaError_t launch_colmax(const float* UT, int64_t I, int64_t I_pad, int C, float* cmax, cudaStream_t s);
 
 }  // namespace tc
 }  // namespace jk

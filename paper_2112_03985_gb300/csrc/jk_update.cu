@@ -41,6 +41,13 @@ __device__ __forceinline__ double load_part(const PT* p) {
   return (double)__ldg(p);
 }
 
+// unevaluated FP32 pair (hi, lo) of the exact-chain tensor-core form
+template <>
+__device__ __forceinline__ double load_part<float2>(const float2* p) {
+  const float2 v = __ldg(p);
+  return (double)v.x + (double)v.y;
+}
+
 template <typename PT>
 __global__ void __launch_bounds__(NTA) update_phase_a(UpdateArgs a) {
   const int g = blockIdx.x, rc = blockIdx.y;
@@ -225,7 +232,21 @@ __global__ void __launch_bounds__(NTB) update_phase_b(UpdateArgs a) {
     for (int64_t t = tid; t < a.I * R; t += NTB) {
       const int r = (int)(t / a.I);
       const int64_t i = t - (int64_t)r * a.I;
-      a.UT[(int64_t)(off + r) * a.I_pad + i] = (float)a.U[i * a.C + off + r];
+      const double u = a.U[i * a.C + off + r];
+      const float hi = (float)u;
+      a.UT[(int64_t)(off + r) * a.I_pad + i] = hi;
+      if (a.UT_lo != nullptr) a.UT_lo[(int64_t)(off + r) * a.I_pad + i] = (float)(u - (double)hi);
+    }
+    if (a.cmax != nullptr) {
+      __syncthreads();
+      const int warp = tid >> 5, lane = tid & 31;
+      for (int r = warp; r < R; r += NTB / 32) {
+        float mx = 0.f;
+        const float* col = a.UT + (int64_t)(off + r) * a.I_pad;
+        for (int64_t i = lane; i < a.I; i += 32) mx = fmaxf(mx, fabsf(col[i]));
+        for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        if (lane == 0) a.cmax[off + r] = mx;
+      }
     }
   }
   if (!last) return;
@@ -344,8 +365,10 @@ __global__ void sum_blocks_kernel(const double* eg, int K, double* out) {
 
 cudaError_t launch_update(const UpdateArgs& a, cudaStream_t s) {
   dim3 ga((unsigned)a.K, (unsigned)a.RC);
-  if (a.part_is_f32)
+  if (a.part_kind == kPartF32)
     update_phase_a<float><<<ga, NTA, 0, s>>>(a);
+  else if (a.part_kind == kPartF32x2)
+    update_phase_a<float2><<<ga, NTA, 0, s>>>(a);
   else
     update_phase_a<double><<<ga, NTA, 0, s>>>(a);
   cudaError_t e = cudaGetLastError();

@@ -97,7 +97,9 @@ def test_tc_als_tracks_oracle_on_cfg1():
             ref = ora.factors[col][n]
             err = np.linalg.norm(U[n][:, offs[g]:offs[g + 1]] - ref) / np.linalg.norm(ref)
             assert err <= 1e-4, (g, n, err)
-        assert np.allclose(L[:, g], ora.losses[:, col], rtol=1e-4)
+        # the efficient error formula cancels ||T||^2 against 2<T, M>, so an MTTKRP
+        # error eps moves e by about 2 eps ||T_g||^2: compare relative to ||T_g||^2
+        assert np.all(np.abs(L[:, g] - ora.losses[:, col]) <= 1e-4 * ora.normT2[col])
 
 
 def test_tc_gradient_matches_oracle():
