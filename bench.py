@@ -41,7 +41,7 @@ def parse():
     p.add_argument("--steps", type=int, default=50)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    p.add_argument("--precision", default="fp64")
+    p.add_argument("--precision", default="exact_bf16")
     p.add_argument("--e2e-reps", type=int, default=3)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-fp64-compare", action="store_true")
@@ -82,6 +82,8 @@ def roofline_peak(precision, peaks):
         return "tensor", bf16, "measured BF16 sustained"
     if precision == "split_bf16":
         return "tensor", bf16 / 6.0, "measured BF16 sustained / 6 passes"
+    if precision == "exact_bf16":
+        return "tensor", bf16 / 10.0, "measured BF16 sustained / 10 BF16 passes (exact-chain slices)"
     raise ValueError(precision)
 
 
