@@ -87,7 +87,10 @@ typedef struct {
                                fail with JKCALS_ERR_OOM (lets callers bound device memory) */
   int kernel_timing;    /* 1: record CUDA events around every MTTKRP launch of a sweep
                            (read with jkcals_kernel_times); 0 (default): off            */
-  int reserved[7];
+  int update_mode;      /* per-block update kernels: 0 (default) automatic, 1 one CTA per
+                           block with the block's rows in shared memory, 2 two-phase
+                           (row chunks, then a per-block reduction)                    */
+  int reserved[6];
 } jkcals_options;
 
 /* Fill *opt with the defaults above. */

@@ -64,7 +64,7 @@ class JKCALS:
     def __init__(self, T, n_hat: int, ranks: Sequence[int], left_out: Sequence[Sequence[int]],
                  init: Sequence, *, precision: str = "fp64", normalise: bool = True,
                  use_graph: bool = True, splits: int = 0, max_device_bytes: int = 0,
-                 kernel_timing: bool = False, stream=None):
+                 kernel_timing: bool = False, update_mode: int = 0, stream=None):
         lib = L.load()
         self._lib = lib
         self._h = ct.c_void_p()
@@ -83,6 +83,7 @@ class JKCALS:
         opt.splits = int(splits)
         opt.max_device_bytes = int(max_device_bytes)
         opt.kernel_timing = int(bool(kernel_timing))
+        opt.update_mode = int(update_mode)
         dims = (ct.c_int64 * self.N)(*self.dims)
         rk = (ct.c_int32 * self.K)(*self.ranks)
         ptr, idx = left_out_csr(left_out)

@@ -146,6 +146,15 @@ void make_plan(jkcals_ctx* h) {
     RC = (I + rpc - 1) / rpc;
     p.upd.rows_per_chunk = (int)rpc;
     p.upd.RC = (int)RC;
+    // fused update: every block's rows fit in shared memory and the blocks fill the GPU
+    p.upd.fused_smem = update_fused_smem(I, h->Rmax);
+    const bool fits = p.upd.fused_smem <= 160 * 1024;
+    if (h->opt.update_mode == 1)
+      p.upd.fused = fits ? 1 : 0;
+    else if (h->opt.update_mode == 2)
+      p.upd.fused = 0;
+    else
+      p.upd.fused = (fits && h->K >= h->num_sms / 2) ? 1 : 0;
   }
 }
 
@@ -340,9 +349,16 @@ jkcals_status enqueue_sweep(jkcals_ctx* h) {
     if (h->opt.kernel_timing) JK_CUDA(h, cudaEventRecordWithFlags(h->ev_start[n], h->stream, cudaEventRecordExternal));
     JK_TRY(enqueue_mttkrp(h, n, h->U, h->UT, h->UTlo, h->cmax));
     if (h->opt.kernel_timing) JK_CUDA(h, cudaEventRecordWithFlags(h->ev_stop[n], h->stream, cudaEventRecordExternal));
-    UpdateArgs a = update_args(h, n, h->part, part_kind(h), mode_splits(h, n));
-    JK_CUDA(h, launch_update(a, h->stream));
-    kernels += 3;
+    // fixed-order split-K reduction into FP64 Mbar_n, then the per-block update
+    JK_TRY(reduce_into(h, n, h->mbuf));
+    UpdateArgs a = update_args(h, n, h->mbuf, kPartF64, 1);
+    if (h->plan[n].upd.fused) {
+      JK_CUDA(h, launch_update_fused(a, h->plan[n].upd.fused_smem, h->Rmax, h->uniform_rank, h->stream));
+      kernels += 3;
+    } else {
+      JK_CUDA(h, launch_update(a, h->stream));
+      kernels += 4;
+    }
   }
   JK_CUDA(h, launch_advance_sweep(h->d_sweep_idx, h->stream));
   h->kernels_per_sweep = kernels + 1;
@@ -468,6 +484,7 @@ jkcals_status create_impl(jkcals_ctx* h, const void* T, int T_dtype, const int32
   }
   h->C = c;
   h->gram_total = go;
+  for (int g = 0; g < K; ++g) h->uniform_rank = h->uniform_rank && (h->R[g] == h->Rmax);
   h->lo_ptr.assign(left_out_ptr, left_out_ptr + K + 1);
   h->lo_idx.assign(left_out_idx, left_out_idx + left_out_ptr[K]);
   for (int g = 0; g < K; ++g) std::sort(h->lo_idx.begin() + h->lo_ptr[g], h->lo_idx.begin() + h->lo_ptr[g + 1]);
@@ -591,7 +608,13 @@ jkcals_status create_impl(jkcals_ctx* h, const void* T, int T_dtype, const int32
       JK_CUDA(h, cudaEventCreate(&h->ev_stop[n]));
     }
   }
-  h->kernels_per_sweep = 3 * N + 1;
+  size_t fsmem = 0;
+  for (int n = 0; n < N; ++n)
+    if (h->plan[n].upd.fused) fsmem = std::max(fsmem, h->plan[n].upd.fused_smem);
+  if (fsmem > 0) JK_CUDA(h, prepare_update_fused(fsmem, h->Rmax, h->uniform_rank));
+  h->kernels_per_sweep = 0;
+  for (int n = 0; n < N; ++n) h->kernels_per_sweep += h->plan[n].upd.fused ? 3 : 4;
+  h->kernels_per_sweep += 1;
   JK_TRY(refresh_factor_state(h));
   JK_CUDA(h, cudaStreamSynchronize(st));
   return JKCALS_OK;
@@ -722,6 +745,7 @@ jkcals_status jkcals_create(jkcals_t* out, int N, const int64_t* dims, const voi
   if (opt) o = *opt;
   if (o.precision < JKCALS_FP64 || o.precision > JKCALS_EXACT_BF16) return fail(JKCALS_ERR_ARG, "bad precision");
   if (o.splits < 0) return fail(JKCALS_ERR_ARG, "splits must be >= 0");
+  if (o.update_mode < 0 || o.update_mode > 2) return fail(JKCALS_ERR_ARG, "update_mode must be 0, 1 or 2");
 
   jkcals_ctx* h = new jkcals_ctx();
   h->N = N;

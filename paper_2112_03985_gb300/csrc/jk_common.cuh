@@ -47,6 +47,8 @@ struct KrpOperands {
 struct UpdatePlan {
   int rows_per_chunk;
   int RC;
+  int fused;          // 1: one CTA per block over the reduced Mbar_n (jk_update_fused.cu)
+  size_t fused_smem;  // its dynamic shared memory
 };
 
 struct ModePlan {
@@ -84,6 +86,7 @@ struct jkcals_ctx {
   int K = 0;
   int C = 0;
   int Rmax = 0;
+  bool uniform_rank = true;  // every block has R_g == Rmax
   jkcals_options opt{};
   cudaStream_t stream = nullptr;
   bool owns_stream = false;
@@ -226,6 +229,10 @@ struct UpdateArgs {
   float* UT_lo;                     // NULL or the low parts fl32(U - UT), refreshed
 };
 cudaError_t launch_update(const UpdateArgs& a, cudaStream_t s);
+// fused one-CTA-per-block update (jk_update_fused.cu); part = reduced Mbar_n (FP64)
+size_t update_fused_smem(int64_t I, int Rmax);
+cudaError_t prepare_update_fused(size_t smem, int Rmax, bool uniform_rank);
+cudaError_t launch_update_fused(const UpdateArgs& a, size_t smem, int Rmax, bool uniform_rank, cudaStream_t s);
 cudaError_t launch_advance_sweep(int* sweep_idx, cudaStream_t s);
 
 // ---- gradient epilogue (jk_update.cu) ----------------------------------------

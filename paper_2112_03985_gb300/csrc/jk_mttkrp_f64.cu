@@ -117,13 +117,31 @@ __global__ void reduce_partials_f64_kernel(const double* __restrict__ part, int 
   }
 }
 
+// Double-float accumulation (unevaluated FP32 pair hi + lo, Knuth TwoSum): about
+// 2^-44 relative, on the FP32 pipe; one conversion to FP64 per output.  GB300
+// issues FP64 (and FP64 conversions) at a small fraction of the FP32 rate, so
+// summing S partials in FP64 would make this reduction FP64-bound.
+__device__ __forceinline__ void df_add(float& hi, float& lo, float x) {
+  const float s = __fadd_rn(hi, x);
+  const float bb = __fsub_rn(s, hi);
+  const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(x, bb));
+  lo = __fadd_rn(lo, e);
+  hi = s;
+}
+
+__device__ __forceinline__ double df_to_double(float hi, float lo) {
+  const float s = __fadd_rn(hi, lo);
+  const float r = __fsub_rn(lo, __fsub_rn(s, hi));
+  return (double)s + (double)r;
+}
+
 __global__ void reduce_partials_f32_kernel(const float* __restrict__ part, int S, int64_t count,
                                            double* __restrict__ out) {
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < count;
        e += (int64_t)gridDim.x * blockDim.x) {
-    double acc = (double)part[e];
-    for (int s = 1; s < S; ++s) acc += (double)part[(int64_t)s * count + e];
-    out[e] = acc;
+    float hi = 0.f, lo = 0.f;
+    for (int s = 0; s < S; ++s) df_add(hi, lo, __ldg(part + (int64_t)s * count + e));
+    out[e] = df_to_double(hi, lo);
   }
 }
 
@@ -131,12 +149,13 @@ __global__ void reduce_partials_f32x2_kernel(const float2* __restrict__ part, in
                                              double* __restrict__ out) {
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < count;
        e += (int64_t)gridDim.x * blockDim.x) {
-    double acc = 0.0;
+    float hi = 0.f, lo = 0.f;
     for (int s = 0; s < S; ++s) {
-      const float2 v = part[(int64_t)s * count + e];
-      acc += (double)v.x + (double)v.y;
+      const float2 v = __ldg(part + (int64_t)s * count + e);
+      df_add(hi, lo, v.x);
+      lo = __fadd_rn(lo, v.y);
     }
-    out[e] = acc;
+    out[e] = df_to_double(hi, lo);
   }
 }
 

@@ -1,0 +1,312 @@
+// Fused per-submodel update, one CTA per block (Alg. 3, the loop over p inside
+// the mode loop), all arithmetic in FP64.  Input: the reduced concurrent
+// MTTKRP Mbar_n (I_n x C, FP64, from the fixed-order split-K reduction).
+//
+//   H = *_{k != n} G^(k)_g ; L L^T = H            (Hadamard line; Cholesky)
+//   x_i = L^-T L^-1 m_i for every row i            (update line)
+//   x_i = 0 for i in D_g when n == n_hat           (zeroing line)
+//   G = sum_i x_i x_i^T                            (Gram refresh)
+//   columns scaled to unit norm if n < N-1         (normalisation reading)
+//   e_g = ||T_{-g}||^2 + sum(H*G) - 2 sum(x*m)     (error line, last mode)
+//
+// The block's rows stay in shared memory between the solve, the Gram and the
+// scaling, so Ubar^(n)_{|g} is written once (FP64 row-major for the update,
+// plus the transposed FP32 hi/lo copies and column maxima that the
+// tensor-core MTTKRP reads).  The Gram is reduced over row groups in a fixed
+// order: deterministic.  Used when every block's rows fit in shared memory and
+// there are enough blocks to fill the GPU; otherwise the two-phase update runs.
+#include <math.h>
+
+#include "jk_common.cuh"
+
+namespace jk {
+namespace {
+
+constexpr int NT = 128;
+
+__device__ __forceinline__ bool left_out(const BlockMeta& bm, int g, int64_t i) {
+  const int64_t b = bm.lo_ptr[g], e = bm.lo_ptr[g + 1];
+  for (int64_t p = b; p < e; ++p)
+    if (bm.lo_idx[p] == i) return true;
+  return false;
+}
+
+// RMAX bounds the rank of every block; FIXED means every block has exactly RMAX
+// components, so the per-rank guards fold away at compile time.
+template <int RMAX, bool FIXED>
+__global__ void __launch_bounds__(NT, FIXED ? 4 : 2) update_fused_kernel(UpdateArgs a) {
+  const int g = blockIdx.x;
+  const int tid = threadIdx.x;
+  const bool last = (a.n == a.N - 1);
+  const int sweep = last ? *a.sweep_idx : 0;
+  const double qnan = __longlong_as_double(0x7ff8000000000000LL);
+  if (a.status[g] != 0) {
+    if (last && tid == 0 && a.loss_hist != nullptr && sweep < a.loss_cap) a.loss_hist[(int64_t)sweep * a.K + g] = qnan;
+    return;
+  }
+  const int R = FIXED ? RMAX : a.bm.R[g];
+  const int off = a.bm.off[g], go = a.bm.gram_off[g];
+  const int64_t I = a.I;
+  const double* M = reinterpret_cast<const double*>(a.part);
+
+  extern __shared__ double X[];             // I x R rows of this block
+  __shared__ double L[RMAX][RMAX + 1];      // H, then its Cholesky factor
+  __shared__ double Hc[RMAX * RMAX];        // H kept for the error
+  __shared__ double G[RMAX][RMAX + 1];
+  __shared__ double invd[RMAX];
+  __shared__ double scale[RMAX];
+  __shared__ double red[NT];
+  __shared__ int spd_ok;
+
+  for (int p = tid; p < R * R; p += NT) {
+    double h = 1.0;
+    for (int k = 0; k < a.N; ++k)
+      if (k != a.n) h *= a.gram[k][go + p];
+    L[p / R][p % R] = h;
+    Hc[p] = h;
+  }
+  if (tid == 0) spd_ok = 1;
+  // this thread's first row of Mbar_n, loaded while warp 0 factorises H
+  double m[RMAX];
+  {
+    const int64_t i = tid;
+#pragma unroll
+    for (int r = 0; r < RMAX; ++r) m[r] = (i < I && r < R) ? M[i * a.C + off + r] : 0.0;
+  }
+  __syncthreads();
+  if (tid < 32) {
+    const int lane = tid;
+    for (int j = 0; j < R; ++j) {
+      if (lane == 0) {
+        double d = L[j][j];
+        for (int k = 0; k < j; ++k) d -= L[j][k] * L[j][k];
+        if (!(d > 0.0) || !isfinite(d)) {
+          spd_ok = 0;
+          d = 1.0;
+        }
+        L[j][j] = sqrt(d);
+        invd[j] = 1.0 / L[j][j];
+      }
+      __syncwarp();
+      const int i = j + 1 + lane;
+      if (i < R) {
+        double v = L[i][j];
+        for (int k = 0; k < j; ++k) v -= L[i][k] * L[j][k];
+        L[i][j] = v * invd[j];
+      }
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  if (!spd_ok) {
+    if (tid == 0) {
+      atomicOr(&a.status[g], (int)JKCALS_BLOCK_NOT_SPD);
+      if (last && a.loss_hist != nullptr && sweep < a.loss_cap) a.loss_hist[(int64_t)sweep * a.K + g] = qnan;
+    }
+    return;
+  }
+
+  // solve every row; keep the rows in shared memory
+  double fit = 0.0;
+  for (int64_t i = tid; i < I; i += NT) {
+    double x[RMAX];
+    if (i != tid) {
+      const double* mrow = M + i * a.C + off;
+#pragma unroll
+      for (int r = 0; r < RMAX; ++r) m[r] = (r < R) ? mrow[r] : 0.0;
+    }
+    if (a.n == a.n_hat && left_out(a.bm, g, i)) {
+#pragma unroll
+      for (int r = 0; r < RMAX; ++r) x[r] = 0.0;
+    } else {
+#pragma unroll
+      for (int r = 0; r < RMAX; ++r) {
+        if (r < R) {
+          double v = m[r];
+#pragma unroll
+          for (int k = 0; k < r; ++k) v -= L[r][k] * x[k];
+          x[r] = v * invd[r];
+        } else {
+          x[r] = 0.0;
+        }
+      }
+#pragma unroll
+      for (int r = RMAX - 1; r >= 0; --r) {
+        if (r < R) {
+          double v = x[r];
+#pragma unroll
+          for (int k = r + 1; k < RMAX; ++k)
+            if (k < R) v -= L[k][r] * x[k];
+          x[r] = v * invd[r];
+        }
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < RMAX; ++r) {
+      if (r < R) {
+        X[i * R + r] = x[r];
+        fit = fma(x[r], m[r], fit);
+      }
+    }
+  }
+  __syncthreads();
+
+  // Gram (upper triangle), row groups reduced in a fixed order
+  const int npairs = R * (R + 1) / 2;
+  const int groups = NT / npairs;
+  if (groups == 0) {
+    // R > 22: one thread per pair, all rows
+    for (int p = tid; p < npairs; p += NT) {
+      int q = p, r0 = 0;
+      while (q >= R - r0) {
+        q -= R - r0;
+        ++r0;
+      }
+      double acc = 0.0;
+      for (int64_t i = 0; i < I; ++i) acc = fma(X[i * R + r0], X[i * R + r0 + q], acc);
+      G[r0][r0 + q] = acc;
+      G[r0 + q][r0] = acc;
+    }
+    __syncthreads();
+  } else {
+    double acc = 0.0;
+    int pr = 0, pc = 0;
+    const int p = tid % npairs, grp = tid / npairs;
+    if (grp < groups) {
+      int q = p;
+      while (q >= R - pr) {
+        q -= R - pr;
+        ++pr;
+      }
+      pc = pr + q;
+      for (int64_t i = grp; i < I; i += groups) acc = fma(X[i * R + pr], X[i * R + pc], acc);
+    }
+    red[tid] = acc;
+    __syncthreads();
+    if (tid < npairs) {
+      double s = 0.0;
+      for (int gg = 0; gg < groups; ++gg) s += red[gg * npairs + tid];
+      int q = tid, r0 = 0;
+      while (q >= R - r0) {
+        q -= R - r0;
+        ++r0;
+      }
+      G[r0][r0 + q] = s;
+      G[r0 + q][r0] = s;
+    }
+    __syncthreads();
+  }
+
+  // normalisation (modes n < N-1): unit columns, norm dropped
+  const bool norm = a.normalise && a.n < a.N - 1;
+  if (tid < R) {
+    double sc = 1.0;
+    if (norm) {
+      const double v = sqrt(G[tid][tid]);
+      sc = (v > 0.0) ? 1.0 / v : 1.0;
+    }
+    scale[tid] = sc;
+  }
+  __syncthreads();
+  if (norm) {
+    for (int p = tid; p < R * R; p += NT) G[p / R][p % R] *= scale[p / R] * scale[p % R];
+    for (int64_t t = tid; t < I * R; t += NT) X[t] *= scale[t % R];
+    __syncthreads();
+  }
+
+  // write the factor block: FP64 row-major, and the transposed FP32 hi/lo copies
+  for (int64_t t = tid; t < I * R; t += NT) {
+    const int64_t i = t / R;
+    const int r = (int)(t - i * R);
+    a.U[i * a.C + off + r] = X[t];
+  }
+  if (a.UT != nullptr) {
+    for (int64_t t = tid; t < I * R; t += NT) {
+      const int r = (int)(t / I);
+      const int64_t i = t - (int64_t)r * I;
+      const double u = X[i * R + r];
+      const float hi = (float)u;
+      a.UT[(int64_t)(off + r) * a.I_pad + i] = hi;
+      if (a.UT_lo != nullptr) a.UT_lo[(int64_t)(off + r) * a.I_pad + i] = (float)(u - (double)hi);
+    }
+    if (a.cmax != nullptr) {
+      const int warp = tid >> 5, lane = tid & 31;
+      for (int r = warp; r < R; r += NT / 32) {
+        float mx = 0.f;
+        for (int64_t i = lane; i < I; i += 32) mx = fmaxf(mx, fabsf((float)X[i * R + r]));
+        for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        if (lane == 0) a.cmax[off + r] = mx;
+      }
+    }
+  }
+  for (int p = tid; p < R * R; p += NT) a.gram_n[go + p] = G[p / R][p % R];
+  if (!last) return;
+
+  // e_g = ||T_{-g}||^2 + sum(H * G) - 2 sum(x * m)
+  __syncthreads();
+  double hg = 0.0;
+  for (int p = tid; p < R * R; p += NT) hg = fma(Hc[p], G[p / R][p % R], hg);
+  red[tid] = hg - 2.0 * fit;
+  __syncthreads();
+  for (int w = NT / 2; w > 0; w >>= 1) {
+    if (tid < w) red[tid] += red[tid + w];
+    __syncthreads();
+  }
+  if (tid == 0) {
+    const double nt = a.normT2[g];
+    const double e = nt + red[0];
+    a.loss_last[g] = e;
+    if (a.loss_hist != nullptr && sweep < a.loss_cap) a.loss_hist[(int64_t)sweep * a.K + g] = e;
+    const double tol = *a.tol;
+    const double prev = a.loss_prev[g];
+    if (tol > 0.0 && isfinite(prev) && fabs(prev - e) / nt < tol) a.status[g] |= JKCALS_BLOCK_CONVERGED;
+    a.loss_prev[g] = e;
+  }
+}
+
+
+size_t update_fused_smem(int64_t I, int Rmax) { return (size_t)I * Rmax * sizeof(double); }
+
+// Instances: exact ranks 1..8 when all blocks share one rank, otherwise the
+// rank classes 8, 16, 32 with per-rank guards.
+template <int RM, bool F>
+cudaError_t run_fused(const UpdateArgs* a, size_t smem, cudaStream_t s, bool prepare) {
+  if (prepare)
+    return cudaFuncSetAttribute(update_fused_kernel<RM, F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  update_fused_kernel<RM, F><<<a->K, NT, smem, s>>>(*a);
+  return cudaGetLastError();
+}
+
+static cudaError_t dispatch_fused(const UpdateArgs* a, size_t smem, int Rmax, bool uniform, cudaStream_t s,
+                                  bool prepare) {
+  if (uniform) {
+    switch (Rmax) {
+      case 1: return run_fused<1, true>(a, smem, s, prepare);
+      case 2: return run_fused<2, true>(a, smem, s, prepare);
+      case 3: return run_fused<3, true>(a, smem, s, prepare);
+      case 4: return run_fused<4, true>(a, smem, s, prepare);
+      case 5: return run_fused<5, true>(a, smem, s, prepare);
+      case 6: return run_fused<6, true>(a, smem, s, prepare);
+      case 7: return run_fused<7, true>(a, smem, s, prepare);
+      case 8: return run_fused<8, true>(a, smem, s, prepare);
+      default: break;
+    }
+  }
+  if (Rmax <= 8) return run_fused<8, false>(a, smem, s, prepare);
+  if (Rmax <= 16) return run_fused<16, false>(a, smem, s, prepare);
+  return run_fused<32, false>(a, smem, s, prepare);
+}
+
+}  // namespace
+
+size_t update_fused_smem(int64_t I, int Rmax) { return (size_t)I * Rmax * sizeof(double); }
+
+cudaError_t prepare_update_fused(size_t smem, int Rmax, bool uniform) {
+  return dispatch_fused(nullptr, smem, Rmax, uniform, nullptr, true);
+}
+
+cudaError_t launch_update_fused(const UpdateArgs& a, size_t smem, int Rmax, bool uniform, cudaStream_t s) {
+  return dispatch_fused(&a, smem, Rmax, uniform, s, false);
+}
+
+}  // namespace jk

@@ -88,18 +88,20 @@ def _als_parity(w, sweeps, blocks=None, device=None, **kw):
     return errs, lrel, st, losses, ora
 
 
-def test_cfg1_fp64_als_parity_50_sweeps():
+@pytest.mark.parametrize("update_mode", [1, 2], ids=["fused", "two_phase"])
+def test_cfg1_fp64_als_parity_50_sweeps(update_mode):
     """Configuration 1: 20x30x40, R=3, 20 LOO + full model, 50 sweeps, FP64."""
     _cuda()
     w = W.make_config(1)
-    errs, lrel, st, losses, ora = _als_parity(w, w.sweeps)
+    errs, lrel, st, losses, ora = _als_parity(w, w.sweeps, update_mode=update_mode)
     assert np.all(st == 0)
     assert errs.max() <= FACTOR_RTOL, errs.max()
     assert lrel.max() <= FACTOR_RTOL, lrel.max()
 
 
-@pytest.mark.parametrize("case", ["4way_nhat2", "delete3", "mixed_ranks", "nhat_last"])
-def test_als_parity_variants(case):
+@pytest.mark.parametrize("update_mode", [1, 2], ids=["fused", "two_phase"])
+@pytest.mark.parametrize("case", ["4way_nhat2", "delete3", "mixed_ranks", "nhat_last", "rank20"])
+def test_als_parity_variants(case, update_mode):
     _cuda()
     if case == "4way_nhat2":
         w = _ragged((6, 5, 7, 4), 2, n_hat=2, seed=7)
@@ -107,9 +109,11 @@ def test_als_parity_variants(case):
         w = _ragged((12, 9, 8), 2, d=3, seed=8)
     elif case == "mixed_ranks":
         w = _ragged((9, 20, 11), 2, ranks=[1, 2, 3, 2, 1, 3, 2, 1, 2, 3], seed=9)
+    elif case == "rank20":
+        w = _ragged((30, 24, 22), 20, seed=18, d=10)
     else:
         w = _ragged((7, 6, 9), 2, n_hat=2, seed=10)
-    errs, lrel, st, _, _ = _als_parity(w, 20)
+    errs, lrel, st, _, _ = _als_parity(w, 20, update_mode=update_mode)
     assert np.all(st == 0)
     assert errs.max() <= FACTOR_RTOL, errs.max()
     assert lrel.max() <= FACTOR_RTOL, lrel.max()
