@@ -49,8 +49,10 @@ namespace {
 
 using namespace ptx;
 
-constexpr int kThreads = 192;
+constexpr int kProducerWarps = 8;                    // two per scheduler: hides load latency
+constexpr int kThreads = 32 * (2 + kProducerWarps);  // + the TMA warp and the MMA warp
 constexpr int kProducerWarp0 = 2;
+constexpr int kRowsPerWarp = 128 / kProducerWarps;   // rows of the A tile per producer warp
 constexpr int kRowsM = 128;   // MMA M
 
 // UMMA shared-memory descriptor: K-major operand, ROW-byte swizzle (128 -> 2,
@@ -137,7 +139,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   constexpr int CHUNK = 16 / Cfg::elem;          // elements per 16-byte chunk
   constexpr int CPR = ROW / 16;                  // chunks per row
   constexpr int RPI = 32 / CPR;                  // rows covered by one warp instruction
-  constexpr int ROWS_PER_THREAD = 32 / RPI;      // rows per producer thread per stage
+  constexpr int ROWS_PER_THREAD = kRowsPerWarp / RPI;  // rows per producer thread per stage
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t a_bytes = kRowsM * ROW;
   const uint32_t b_bytes = (uint32_t)a.BN * ROW;
@@ -160,7 +162,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
-      mbar_init(&full_a[s], 32 * 4);
+      mbar_init(&full_a[s], 32 * kProducerWarps);
       mbar_init(&full_b[s], 1);
       mbar_init(&empty[s], 1);
     }
@@ -237,7 +239,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
   } else {
     // ---------------- Khatri-Rao producers (warps 2..5) ------------------------------
-    const int pw = warp - kProducerWarp0;   // 0..3
+    const int pw = warp - kProducerWarp0;   // 0..kProducerWarps-1
     const int rg = lane / CPR;              // row within a group of RPI rows
     const int q = lane % CPR;               // 16-byte chunk within the row
     // per-row scale of the exact-chain form: 2^(7 - E_c)
@@ -246,7 +248,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     for (int rr = 0; rr < ROWS_PER_THREAD; ++rr) {
       rscale[rr] = 1.f;
       if constexpr (Cfg::exact) {
-        const int c = c0 + pw * 32 + rr * RPI + rg;
+        const int c = c0 + pw * kRowsPerWarp + rr * RPI + rg;
         if (c < a.C) {
           double b = (double)__ldg(a.cmax_a + c);
 #pragma unroll
@@ -281,9 +283,9 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
         }
       }
-#pragma unroll 2
+#pragma unroll
       for (int rr = 0; rr < ROWS_PER_THREAD; ++rr) {
-        const int m = pw * 32 + rr * RPI + rg;   // row of the A tile = column c0 + m
+        const int m = pw * kRowsPerWarp + rr * RPI + rg;   // row of the A tile = column c0 + m
         const int c = c0 + m;
         float v[CHUNK], vl[CHUNK];
 #pragma unroll
@@ -373,6 +375,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     have = __all_sync(0xffffffffu, have);   // tcgen05.ld is warp-collective
     tc_fence_after();
     const int quarter = warp & 3;             // TMEM lanes 32*quarter .. +31
+    const int half = (warp - kProducerWarp0) >> 2;   // two warps per lane quarter split the columns
     const int m = quarter * 32 + lane;
     const int c = c0 + m;
     int Ec = 0;
@@ -387,7 +390,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     float* out = a.part + (int64_t)blockIdx.z * a.I * a.C;
     const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16);
-    for (int cc = 0; cc < a.BN; cc += 32) {
+    for (int cc = 32 * half; cc < a.BN; cc += 64) {
       const int width = (a.BN - cc >= 32) ? 32 : 16;
       uint32_t v[32];
       if constexpr (!Cfg::exact) {
