@@ -176,6 +176,8 @@ jkcals_status make_tc_plan(jkcals_ctx* h) {
     p.a_mode = (n == 0) ? 1 : 0;
     p.Ia_pad = (int)round_up(h->dims[p.a_mode], chunk);
     p.Jp = (int64_t)p.Ia_pad * (h->J[n] / h->dims[p.a_mode]);
+    if (p.Jp > 2147483647LL - 4096)   // the kernel indexes columns in 32 bits
+      return fail(JKCALS_ERR_UNSUPPORTED, "tensor-core forms need prod of the other dims < 2^31");
     const int64_t nt = (I + bn_max - 1) / bn_max;
     p.BN = (int)round_up((I + nt - 1) / nt, 16);
     p.tiles_c = (h->C + 127) / 128;

@@ -238,23 +238,64 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (!ok) wait_drain(accum, 0);
     }
   } else {
-    // ---------------- Khatri-Rao producers (warps 2..5) ------------------------------
+    // ---------------- Khatri-Rao producers (warps 2..) -------------------------------
     const int pw = warp - kProducerWarp0;   // 0..kProducerWarps-1
     const int rg = lane / CPR;              // row within a group of RPI rows
     const int q = lane % CPR;               // 16-byte chunk within the row
-    // per-row scale of the exact-chain form: 2^(7 - E_c)
+    // per-row constants, hoisted out of the k loop: validity, global row
+    // pointers of the factor copies, the swizzled shared-memory offset and the
+    // exact-chain scale 2^(7 - E_c)
+    bool cval[ROWS_PER_THREAD];
     float rscale[ROWS_PER_THREAD];
+    uint32_t soff[ROWS_PER_THREAD];
+    const float* ra[ROWS_PER_THREAD];
+    const float* ral[ROWS_PER_THREAD];
+    const float* rq0[ROWS_PER_THREAD];
+    const float* rq0l[ROWS_PER_THREAD];
+    const float* rq1[ROWS_PER_THREAD];
+    const float* rq1l[ROWS_PER_THREAD];
 #pragma unroll
     for (int rr = 0; rr < ROWS_PER_THREAD; ++rr) {
+      const int m = pw * kRowsPerWarp + rr * RPI + rg;   // row of the A tile = column c0 + m
+      const int c = c0 + m;
+      cval[rr] = c < a.C;
+      const int cc = cval[rr] ? c : 0;
+      const int sw = (ROW == 128) ? (m & 7) : ((m >> 1) & 3);
+      soff[rr] = (uint32_t)(m >> 3) * (8u * ROW) + (uint32_t)(m & 7) * ROW + (uint32_t)((q ^ sw) << 4);
+      ra[rr] = a.UTa + (int64_t)cc * a.Ia_pad;
+      ral[rr] = Cfg::exact ? a.UTa_lo + (int64_t)cc * a.Ia_pad : nullptr;
+      rq0[rr] = a.nq > 0 ? a.UTq[0] + (int64_t)cc * a.qpad[0] : nullptr;
+      rq0l[rr] = (Cfg::exact && a.nq > 0) ? a.UTq_lo[0] + (int64_t)cc * a.qpad[0] : nullptr;
+      rq1[rr] = a.nq > 1 ? a.UTq[1] + (int64_t)cc * a.qpad[1] : nullptr;
+      rq1l[rr] = (Cfg::exact && a.nq > 1) ? a.UTq_lo[1] + (int64_t)cc * a.qpad[1] : nullptr;
       rscale[rr] = 1.f;
       if constexpr (Cfg::exact) {
-        const int c = c0 + pw * kRowsPerWarp + rr * RPI + rg;
-        if (c < a.C) {
+        if (cval[rr]) {
           double b = (double)__ldg(a.cmax_a + c);
 #pragma unroll
           for (int t = 0; t < kMaxModes - 2; ++t)
             if (t < a.nq) b *= (double)__ldg(a.cmax_q[t] + c);
           rscale[rr] = pow2f(7 - bound_exponent(b));
+        }
+      }
+    }
+    // this thread's column j of the unfolding: j = ia + Ia_pad * o, o mixed-radix
+    // over the remaining modes; advanced incrementally by BK per k-step
+    const int je32 = (int)je;
+    int jcur = (int)jb + q * CHUNK;
+    int ia = 0;
+    int iq[kMaxModes - 2];
+    {
+      const int o = jcur / a.Ia_pad;
+      ia = jcur - o * a.Ia_pad;
+      int rem = o;
+#pragma unroll
+      for (int t = 0; t < kMaxModes - 2; ++t) {
+        iq[t] = 0;
+        if (t < a.nq) {
+          const int qq = rem / a.qdims[t];
+          iq[t] = rem - qq * a.qdims[t];
+          rem = qq;
         }
       }
     }
@@ -266,37 +307,21 @@ __global__ void __launch_bounds__(kThreads, 1)
         ok = false;
         break;
       }
-      const int64_t j = jb + (int64_t)it * BK + q * CHUNK;
-      const bool jvalid = j < je;
-      int ia = 0;
-      int iq[kMaxModes - 2];
-      if (jvalid) {
-        const int64_t o = j / a.Ia_pad;
-        ia = (int)(j - o * a.Ia_pad);
-        int64_t rem = o;
-#pragma unroll
-        for (int t = 0; t < kMaxModes - 2; ++t) {
-          if (t < a.nq) {
-            const int64_t qq = rem / a.qdims[t];
-            iq[t] = (int)(rem - qq * a.qdims[t]);
-            rem = qq;
-          }
-        }
-      }
+      const bool jvalid = jcur < je32;
 #pragma unroll
       for (int rr = 0; rr < ROWS_PER_THREAD; ++rr) {
-        const int m = pw * kRowsPerWarp + rr * RPI + rg;   // row of the A tile = column c0 + m
-        const int c = c0 + m;
         float v[CHUNK], vl[CHUNK];
 #pragma unroll
         for (int e = 0; e < CHUNK; ++e) v[e] = vl[e] = 0.f;
-        if (jvalid && c < a.C) {
+        if (jvalid && cval[rr]) {
           if constexpr (!Cfg::exact) {
             float qv = 1.f;
+            if (a.nq > 0) qv = __ldg(rq0[rr] + iq[0]);
+            if (a.nq > 1) qv *= __ldg(rq1[rr] + iq[1]);
 #pragma unroll
-            for (int t = 0; t < kMaxModes - 2; ++t)
-              if (t < a.nq) qv *= __ldg(a.UTq[t] + (int64_t)c * a.qpad[t] + iq[t]);
-            const float4* src = reinterpret_cast<const float4*>(a.UTa + (int64_t)c * a.Ia_pad + ia);
+            for (int t = 2; t < kMaxModes - 2; ++t)
+              if (t < a.nq) qv *= __ldg(a.UTq[t] + (int64_t)(c0 + pw * kRowsPerWarp + rr * RPI + rg) * a.qpad[t] + iq[t]);
+            const float4* src = reinterpret_cast<const float4*>(ra[rr] + ia);
 #pragma unroll
             for (int e4 = 0; e4 < CHUNK / 4; ++e4) {
               const float4 u = __ldg(src + e4);
@@ -312,16 +337,26 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
             for (int t = 0; t < kMaxModes - 2; ++t) {
               if (t < a.nq) {
-                const int64_t idx = (int64_t)c * a.qpad[t] + iq[t];
-                const float bh = __ldg(a.UTq[t] + idx), bl = __ldg(a.UTq_lo[t] + idx);
+                float bh, bl;
+                if (t == 0) {
+                  bh = __ldg(rq0[rr] + iq[0]);
+                  bl = __ldg(rq0l[rr] + iq[0]);
+                } else if (t == 1) {
+                  bh = __ldg(rq1[rr] + iq[1]);
+                  bl = __ldg(rq1l[rr] + iq[1]);
+                } else {
+                  const int64_t idx = (int64_t)(c0 + pw * kRowsPerWarp + rr * RPI + rg) * a.qpad[t] + iq[t];
+                  bh = __ldg(a.UTq[t] + idx);
+                  bl = __ldg(a.UTq_lo[t] + idx);
+                }
                 const float pq = __fmul_rn(qh, bh);
                 const float eq = __fadd_rn(__fmaf_rn(qh, bh, -pq), __fmaf_rn(qh, bl, __fmul_rn(ql, bh)));
                 qh = pq;
                 ql = eq;
               }
             }
-            const float4* src = reinterpret_cast<const float4*>(a.UTa + (int64_t)c * a.Ia_pad + ia);
-            const float4* srcl = reinterpret_cast<const float4*>(a.UTa_lo + (int64_t)c * a.Ia_pad + ia);
+            const float4* src = reinterpret_cast<const float4*>(ra[rr] + ia);
+            const float4* srcl = reinterpret_cast<const float4*>(ral[rr] + ia);
 #pragma unroll
             for (int e4 = 0; e4 < CHUNK / 4; ++e4) {
               const float4 u = __ldg(src + e4), ul = __ldg(srcl + e4);
@@ -335,8 +370,6 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
           }
         }
-        const int sw = (ROW == 128) ? (m & 7) : ((m >> 1) & 3);
-        const uint32_t off = (uint32_t)(m >> 3) * (8u * ROW) + (uint32_t)(m & 7) * ROW + (uint32_t)((q ^ sw) << 4);
         float parts[NS][CHUNK];
 #pragma unroll
         for (int e = 0; e < CHUNK; ++e) {
@@ -363,7 +396,20 @@ __global__ void __launch_bounds__(kThreads, 1)
             w.z = *reinterpret_cast<uint32_t*>(&b2);
             w.w = *reinterpret_cast<uint32_t*>(&b3);
           }
-          *reinterpret_cast<uint4*>(a_tile(s, p) + off) = w;
+          *reinterpret_cast<uint4*>(a_tile(s, p) + soff[rr]) = w;
+        }
+      }
+      // advance this thread's column by BK: carry i_a into the remaining modes
+      jcur += BK;
+      ia += BK;
+      while (ia >= a.Ia_pad) {
+        ia -= a.Ia_pad;
+#pragma unroll
+        for (int t = 0; t < kMaxModes - 2; ++t) {
+          if (t < a.nq) {
+            if (++iq[t] < a.qdims[t]) break;
+            iq[t] = 0;
+          }
         }
       }
       fence_async_shared();
