@@ -173,7 +173,11 @@ jkcals_status make_tc_plan(jkcals_ctx* h) {
     const int64_t I = h->dims[n];
     p.nsplit = nsplit;
     p.row_bytes = row;
-    p.a_mode = (n == 0) ? 1 : 0;
+    // fastest column mode: the smallest other mode, so that its factor rows for
+    // one 128-column tile can sit in shared memory
+    p.a_mode = -1;
+    for (int k = 0; k < h->N; ++k)
+      if (k != n && (p.a_mode < 0 || h->dims[k] < h->dims[p.a_mode])) p.a_mode = k;
     p.Ia_pad = (int)round_up(h->dims[p.a_mode], chunk);
     p.Jp = (int64_t)p.Ia_pad * (h->J[n] / h->dims[p.a_mode]);
     if (p.Jp > 2147483647LL - 4096)   // the kernel indexes columns in 32 bits
@@ -184,7 +188,14 @@ jkcals_status make_tc_plan(jkcals_ctx* h) {
     p.tiles_n = (int)((I + p.BN - 1) / p.BN);
     const size_t stage = (size_t)nsplit * ((size_t)128 * row + (size_t)p.BN * row);
     const size_t budget = 227 * 1024 - 2048;
-    p.stages = (int)std::min<size_t>(4, budget / stage);
+    // the mode-a factor rows of the CTA's 128 columns, staged once per CTA when
+    // they fit beside at least two pipeline stages
+    p.ua_parts = exact ? 2 : 1;
+    p.ua_stride = p.Ia_pad + 4;   // 16-byte skew between rows: fewer bank conflicts
+    const size_t ua_bytes = (size_t)p.ua_parts * 128 * p.ua_stride * sizeof(float);
+    p.ua_smem = (2 * stage + ua_bytes <= budget) ? 1 : 0;
+    const size_t avail = budget - (p.ua_smem ? ua_bytes : 0);
+    p.stages = (int)std::min<size_t>(4, avail / stage);
     if (p.stages < 2) return fail(JKCALS_ERR_UNSUPPORTED, "tensor-core tile does not fit shared memory");
     p.acc_cols = (int)round_up(p.BN, 32);
     p.tmem_cols = 32;
@@ -323,6 +334,8 @@ jkcals_status enqueue_mttkrp(jkcals_ctx* h, int n, double* const* U, float* cons
   a.part = static_cast<float*>(h->part);
   a.err = h->d_err;
   a.rowexp = h->rowexp[n];
+  a.ua_smem = p.ua_smem;
+  a.ua_stride = p.ua_stride;
   JK_CUDA(h, tc::launch_mttkrp_tc(h->opt.precision, p, h->tmap[n], a, h->stream));
   return JKCALS_OK;
 }
@@ -554,8 +567,23 @@ jkcals_status create_impl(jkcals_ctx* h, const void* T, int T_dtype, const int32
       }
       JK_TRY(dalloc_t(h, &h->rowexp[n], (size_t)h->dims[n]));
       JK_CUDA(h, tc::launch_row_exponent(h->Tn64[n], h->dims[n], h->J[n], h->rowexp[n], st));
+      tc::UnfoldMap mp{};
+      {
+        int64_t stride = 1;
+        for (int k = 0; k < N; ++k) {
+          if (k == n) continue;
+          if (k == p.a_mode) {
+            mp.sa = stride;
+          } else {
+            mp.qd[mp.nq] = h->dims[k];
+            mp.qs[mp.nq] = stride;
+            ++mp.nq;
+          }
+          stride *= h->dims[k];
+        }
+      }
       JK_CUDA(h, tc::launch_split_unfold(h->opt.precision, h->Tn64[n], h->dims[n], h->J[n],
-                                         h->dims[p.a_mode], p.Ia_pad, p.Jp, h->rowexp[n], parts, st));
+                                         h->dims[p.a_mode], p.Ia_pad, p.Jp, mp, h->rowexp[n], parts, st));
       h->Ipad[n] = round_up(h->dims[n], chunk);
     }
     JK_CUDA(h, cudaStreamSynchronize(st));

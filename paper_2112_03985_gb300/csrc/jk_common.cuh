@@ -73,6 +73,9 @@ struct TcPlan {
   int Ia_pad;      // its padded size
   int64_t Jp;      // padded columns of the unfolding
   int64_t kchunk;  // padded columns per split (multiple of the k-step)
+  int ua_smem;     // 1: the CTA keeps its 128 factor rows of mode a (hi, lo) in shared memory
+  int ua_stride;   // floats per staged row (Ia_pad plus a bank skew)
+  int ua_parts;    // staged copies: 1 (hi) or 2 (hi, lo)
 };
 }  // namespace tc
 

@@ -145,7 +145,11 @@ __global__ void __launch_bounds__(kThreads, 1)
   const uint32_t b_bytes = (uint32_t)a.BN * ROW;
   const uint32_t stage_bytes = NS * (a_bytes + b_bytes);
   const int STAGES = a.stages;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + (size_t)STAGES * stage_bytes);
+  // staged mode-a factor rows (hi, then lo for the exact-chain form) follow the stages
+  float* ua_hi = reinterpret_cast<float*>(smem + (size_t)STAGES * stage_bytes);
+  const size_t ua_floats = a.ua_smem ? (size_t)kRowsM * a.ua_stride : 0;
+  float* ua_lo = ua_hi + ua_floats;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(ua_hi + ua_floats * (Cfg::exact ? 2 : 1));
   uint64_t* full_a = bars;
   uint64_t* full_b = bars + STAGES;
   uint64_t* empty = bars + 2 * STAGES;
@@ -279,6 +283,32 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
       }
     }
+    if (a.ua_smem) {
+      // stage the CTA's 128 factor rows of mode a once; the k loop then reads
+      // them from shared memory instead of L2
+      const int ptid = threadIdx.x - 32 * kProducerWarp0;
+      const int n4 = a.Ia_pad / 4;
+      for (int idx = ptid; idx < kRowsM * n4; idx += 32 * kProducerWarps) {
+        const int row = idx / n4, col = (idx - row * n4) * 4;
+        const int c = c0 + row;
+        float4 hv = make_float4(0.f, 0.f, 0.f, 0.f), lv = hv;
+        if (c < a.C) {
+          hv = __ldg(reinterpret_cast<const float4*>(a.UTa + (int64_t)c * a.Ia_pad + col));
+          if constexpr (Cfg::exact) lv = __ldg(reinterpret_cast<const float4*>(a.UTa_lo + (int64_t)c * a.Ia_pad + col));
+        }
+        *reinterpret_cast<float4*>(ua_hi + (size_t)row * a.ua_stride + col) = hv;
+        if constexpr (Cfg::exact) *reinterpret_cast<float4*>(ua_lo + (size_t)row * a.ua_stride + col) = lv;
+      }
+      asm volatile("bar.sync 1, %0;" ::"r"(32 * kProducerWarps) : "memory");   // producer warps only
+#pragma unroll
+      for (int rr = 0; rr < ROWS_PER_THREAD; ++rr) {
+        const int m = pw * kRowsPerWarp + rr * RPI + rg;
+        ra[rr] = ua_hi + (size_t)m * a.ua_stride;
+        ral[rr] = ua_lo + (size_t)m * a.ua_stride;
+      }
+    }
+    float qhc[ROWS_PER_THREAD], qlc[ROWS_PER_THREAD];   // cached remaining-mode products
+    bool qstale = true;
     // this thread's column j of the unfolding: j = ia + Ia_pad * o, o mixed-radix
     // over the remaining modes; advanced incrementally by BK per k-step
     const int je32 = (int)je;
@@ -308,6 +338,45 @@ __global__ void __launch_bounds__(kThreads, 1)
         break;
       }
       const bool jvalid = jcur < je32;
+      if (qstale && jvalid) {
+        // product of the remaining modes' factor entries for each row: it only
+        // changes when the column index carries out of mode a
+#pragma unroll
+        for (int rr = 0; rr < ROWS_PER_THREAD; ++rr) {
+          float qh = 1.f, ql = 0.f;
+          if (cval[rr]) {
+#pragma unroll
+            for (int t = 0; t < kMaxModes - 2; ++t) {
+              if (t < a.nq) {
+                float bh, bl = 0.f;
+                if (t == 0) {
+                  bh = __ldg(rq0[rr] + iq[0]);
+                  if constexpr (Cfg::exact) bl = __ldg(rq0l[rr] + iq[0]);
+                } else if (t == 1) {
+                  bh = __ldg(rq1[rr] + iq[1]);
+                  if constexpr (Cfg::exact) bl = __ldg(rq1l[rr] + iq[1]);
+                } else {
+                  const int64_t idx = (int64_t)(c0 + pw * kRowsPerWarp + rr * RPI + rg) * a.qpad[t] + iq[t];
+                  bh = __ldg(a.UTq[t] + idx);
+                  if constexpr (Cfg::exact) bl = __ldg(a.UTq_lo[t] + idx);
+                }
+                if constexpr (Cfg::exact) {
+                  // error-free product of the pairs (qh + ql)(bh + bl)
+                  const float pq = __fmul_rn(qh, bh);
+                  const float eq = __fadd_rn(__fmaf_rn(qh, bh, -pq), __fmaf_rn(qh, bl, __fmul_rn(ql, bh)));
+                  qh = pq;
+                  ql = eq;
+                } else {
+                  qh *= bh;
+                }
+              }
+            }
+          }
+          qhc[rr] = qh;
+          qlc[rr] = ql;
+        }
+        qstale = false;
+      }
 #pragma unroll
       for (int rr = 0; rr < ROWS_PER_THREAD; ++rr) {
         float v[CHUNK], vl[CHUNK];
@@ -315,16 +384,11 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int e = 0; e < CHUNK; ++e) v[e] = vl[e] = 0.f;
         if (jvalid && cval[rr]) {
           if constexpr (!Cfg::exact) {
-            float qv = 1.f;
-            if (a.nq > 0) qv = __ldg(rq0[rr] + iq[0]);
-            if (a.nq > 1) qv *= __ldg(rq1[rr] + iq[1]);
-#pragma unroll
-            for (int t = 2; t < kMaxModes - 2; ++t)
-              if (t < a.nq) qv *= __ldg(a.UTq[t] + (int64_t)(c0 + pw * kRowsPerWarp + rr * RPI + rg) * a.qpad[t] + iq[t]);
+            const float qv = qhc[rr];
             const float4* src = reinterpret_cast<const float4*>(ra[rr] + ia);
 #pragma unroll
             for (int e4 = 0; e4 < CHUNK / 4; ++e4) {
-              const float4 u = __ldg(src + e4);
+              const float4 u = src[e4];   // generic load: shared (staged rows) or global
               v[4 * e4 + 0] = u.x * qv;
               v[4 * e4 + 1] = u.y * qv;
               v[4 * e4 + 2] = u.z * qv;
@@ -333,33 +397,12 @@ __global__ void __launch_bounds__(kThreads, 1)
           } else {
             // Khatri-Rao entry as an unevaluated pair (v + vl) from hi/lo factor
             // copies: error-free products (FMA) keep it to ~2^-44 relative
-            float qh = 1.f, ql = 0.f;
-#pragma unroll
-            for (int t = 0; t < kMaxModes - 2; ++t) {
-              if (t < a.nq) {
-                float bh, bl;
-                if (t == 0) {
-                  bh = __ldg(rq0[rr] + iq[0]);
-                  bl = __ldg(rq0l[rr] + iq[0]);
-                } else if (t == 1) {
-                  bh = __ldg(rq1[rr] + iq[1]);
-                  bl = __ldg(rq1l[rr] + iq[1]);
-                } else {
-                  const int64_t idx = (int64_t)(c0 + pw * kRowsPerWarp + rr * RPI + rg) * a.qpad[t] + iq[t];
-                  bh = __ldg(a.UTq[t] + idx);
-                  bl = __ldg(a.UTq_lo[t] + idx);
-                }
-                const float pq = __fmul_rn(qh, bh);
-                const float eq = __fadd_rn(__fmaf_rn(qh, bh, -pq), __fmaf_rn(qh, bl, __fmul_rn(ql, bh)));
-                qh = pq;
-                ql = eq;
-              }
-            }
+            const float qh = qhc[rr], ql = qlc[rr];
             const float4* src = reinterpret_cast<const float4*>(ra[rr] + ia);
             const float4* srcl = reinterpret_cast<const float4*>(ral[rr] + ia);
 #pragma unroll
             for (int e4 = 0; e4 < CHUNK / 4; ++e4) {
-              const float4 u = __ldg(src + e4), ul = __ldg(srcl + e4);
+              const float4 u = src[e4], ul = srcl[e4];   // generic loads: shared or global
               const float uh4[4] = {u.x, u.y, u.z, u.w}, ul4[4] = {ul.x, ul.y, ul.z, ul.w};
 #pragma unroll
               for (int k = 0; k < 4; ++k) {
@@ -404,6 +447,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       ia += BK;
       while (ia >= a.Ia_pad) {
         ia -= a.Ia_pad;
+        qstale = true;
 #pragma unroll
         for (int t = 0; t < kMaxModes - 2; ++t) {
           if (t < a.nq) {
@@ -598,7 +642,8 @@ int form_passes(int precision) {
 size_t tc_smem_bytes(const TcPlan& p) {
   const size_t row = (size_t)p.row_bytes;
   const size_t stage = (size_t)p.nsplit * (kRowsM * row + (size_t)p.BN * row);
-  return 1024 /*alignment slack*/ + (size_t)p.stages * stage + (3 * p.stages + 1) * 8 + 16;
+  const size_t ua = p.ua_smem ? (size_t)p.ua_parts * kRowsM * p.ua_stride * sizeof(float) : 0;
+  return 1024 /*alignment slack*/ + (size_t)p.stages * stage + ua + (3 * p.stages + 1) * 8 + 16;
 }
 
 cudaError_t prepare_mttkrp_tc(int precision, size_t max_smem) {

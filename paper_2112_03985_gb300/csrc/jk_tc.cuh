@@ -44,6 +44,8 @@ struct TcArgs {
   const float* cmax_a;             // C: max_i |UT_a[c][i]|
   const float* cmax_q[kMaxModes - 2];
   const int* rowexp;               // I_n: F_i of this mode's unfolding
+  int ua_smem;                     // stage the 128 rows of UTa (and UTa_lo) in shared memory
+  int ua_stride;                   // floats per staged row
 };
 
 int form_nsplit(int precision);
@@ -61,10 +63,18 @@ cudaError_t launch_mttkrp_tc(int precision, const TcPlan& p, const CUtensorMap* 
 // create-time conversions (jk_tc_prep.cu)
 // rowexp[i] = smallest F with max_j |Tn64(i, j)| < 2^F (0 for an all-zero row)
 cudaError_t launch_row_exponent(const double* Tn64, int64_t I, int64_t J, int* rowexp, cudaStream_t s);
+// Column map of a padded unfolding: Kolda stride sa of the fastest mode a, and
+// sizes qd / Kolda strides qs of the remaining modes in increasing order.
+struct UnfoldMap {
+  int64_t sa;
+  int nq;
+  int64_t qd[kMaxModes - 2];
+  int64_t qs[kMaxModes - 2];
+};
 // split (and for the exact form slice, using rowexp) the padded unfolding into its parts
 cudaError_t launch_split_unfold(int precision, const double* Tn64, int64_t I, int64_t J, int64_t Ia,
-                                int64_t Ia_pad, int64_t Jp, const int* rowexp, void* const* parts,
-                                cudaStream_t s);
+                                int64_t Ia_pad, int64_t Jp, const UnfoldMap& mp, const int* rowexp,
+                                void* const* parts, cudaStream_t s);
 // UT[c][i] = fl32(U[i][c]); if UT_lo != NULL also UT_lo[c][i] = fl32(U[i][c] - UT[c][i])
 cudaError_t launch_factor_to_ut(const double* U, int64_t I, int C, float* UT, float* UT_lo, int64_t I_pad,
                                 cudaStream_t s);

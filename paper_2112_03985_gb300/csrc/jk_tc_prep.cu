@@ -34,12 +34,14 @@ __global__ void row_exponent_kernel(const double* __restrict__ Tn, int64_t J, in
   }
 }
 
-// parts[p][i * Jp + jp] = part p of T_(n)(i, ia + Ia * o), jp = ia + Ia_pad * o,
+// parts[p][i * Jp + jp] = part p of T_(n)(i, j) with jp = ia + Ia_pad * o: ia is
+// the index of the fastest mode a, o runs mixed-radix over the remaining modes
+// in increasing order, and j is the Eq. kolda_mapping column of those indices;
 // zero where ia >= Ia.  Splits are taken from the FP64 value.
 template <int PREC>
 __global__ void split_unfold_kernel(const double* __restrict__ Tn, int64_t I, int64_t J, int64_t Ia,
-                                    int64_t Ia_pad, int64_t Jp, const int* __restrict__ rowexp, void* p0,
-                                    void* p1, void* p2, void* p3) {
+                                    int64_t Ia_pad, int64_t Jp, UnfoldMap mp, const int* __restrict__ rowexp,
+                                    void* p0, void* p1, void* p2, void* p3) {
   const int64_t total = I * Jp;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
        e += (int64_t)gridDim.x * blockDim.x) {
@@ -47,7 +49,16 @@ __global__ void split_unfold_kernel(const double* __restrict__ Tn, int64_t I, in
     const int64_t jp = e - i * Jp;
     const int64_t o = jp / Ia_pad;
     const int64_t ia = jp - o * Ia_pad;
-    const double x = (ia < Ia) ? Tn[i * J + ia + Ia * o] : 0.0;
+    double x = 0.0;
+    if (ia < Ia) {
+      int64_t j = ia * mp.sa, rem = o;
+      for (int t = 0; t < mp.nq; ++t) {
+        const int64_t qq = rem / mp.qd[t];
+        j += (rem - qq * mp.qd[t]) * mp.qs[t];
+        rem = qq;
+      }
+      x = Tn[i * J + j];
+    }
     if constexpr (PREC == JKCALS_TF32 || PREC == JKCALS_3XTF32) {
       const float h = tf32_rna((float)x);
       static_cast<float*>(p0)[e] = h;
@@ -119,28 +130,28 @@ cudaError_t launch_row_exponent(const double* Tn64, int64_t I, int64_t J, int* r
 }
 
 cudaError_t launch_split_unfold(int precision, const double* Tn64, int64_t I, int64_t J, int64_t Ia,
-                                int64_t Ia_pad, int64_t Jp, const int* rowexp, void* const* parts,
-                                cudaStream_t s) {
+                                int64_t Ia_pad, int64_t Jp, const UnfoldMap& mp, const int* rowexp,
+                                void* const* parts, cudaStream_t s) {
   const unsigned g = grid_for(I * Jp);
   switch (precision) {
     case JKCALS_TF32:
-      split_unfold_kernel<JKCALS_TF32><<<g, 256, 0, s>>>(Tn64, I, J, Ia, Ia_pad, Jp, rowexp, parts[0], nullptr,
+      split_unfold_kernel<JKCALS_TF32><<<g, 256, 0, s>>>(Tn64, I, J, Ia, Ia_pad, Jp, mp, rowexp, parts[0], nullptr,
                                                          nullptr, nullptr);
       break;
     case JKCALS_3XTF32:
-      split_unfold_kernel<JKCALS_3XTF32><<<g, 256, 0, s>>>(Tn64, I, J, Ia, Ia_pad, Jp, rowexp, parts[0],
+      split_unfold_kernel<JKCALS_3XTF32><<<g, 256, 0, s>>>(Tn64, I, J, Ia, Ia_pad, Jp, mp, rowexp, parts[0],
                                                            parts[1], nullptr, nullptr);
       break;
     case JKCALS_BF16:
-      split_unfold_kernel<JKCALS_BF16><<<g, 256, 0, s>>>(Tn64, I, J, Ia, Ia_pad, Jp, rowexp, parts[0], nullptr,
+      split_unfold_kernel<JKCALS_BF16><<<g, 256, 0, s>>>(Tn64, I, J, Ia, Ia_pad, Jp, mp, rowexp, parts[0], nullptr,
                                                          nullptr, nullptr);
       break;
     case JKCALS_SPLIT_BF16:
-      split_unfold_kernel<JKCALS_SPLIT_BF16><<<g, 256, 0, s>>>(Tn64, I, J, Ia, Ia_pad, Jp, rowexp, parts[0],
+      split_unfold_kernel<JKCALS_SPLIT_BF16><<<g, 256, 0, s>>>(Tn64, I, J, Ia, Ia_pad, Jp, mp, rowexp, parts[0],
                                                                parts[1], parts[2], nullptr);
       break;
     case JKCALS_EXACT_BF16:
-      split_unfold_kernel<JKCALS_EXACT_BF16><<<g, 256, 0, s>>>(Tn64, I, J, Ia, Ia_pad, Jp, rowexp, parts[0],
+      split_unfold_kernel<JKCALS_EXACT_BF16><<<g, 256, 0, s>>>(Tn64, I, J, Ia, Ia_pad, Jp, mp, rowexp, parts[0],
                                                                parts[1], parts[2], parts[3]);
       break;
     default:
