@@ -160,7 +160,9 @@ void make_plan(jkcals_ctx* h) {
 
 int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 
-// Tensor-core plan of every mode: N tile, split-K factor, pipeline depth.
+// Tensor-core plan of every mode: N tile, split-K factor, pipeline depths.
+constexpr size_t kSmemOptin = 227 * 1024;   // dynamic shared memory per CTA (opt-in limit)
+
 jkcals_status make_tc_plan(jkcals_ctx* h) {
   const int prec = h->opt.precision;
   const bool exact = prec == JKCALS_EXACT_BF16;
@@ -186,17 +188,28 @@ jkcals_status make_tc_plan(jkcals_ctx* h) {
     p.BN = (int)round_up((I + nt - 1) / nt, 16);
     p.tiles_c = (h->C + 127) / 128;
     p.tiles_n = (int)((I + p.BN - 1) / p.BN);
-    const size_t stage = (size_t)nsplit * ((size_t)128 * row + (size_t)p.BN * row);
-    const size_t budget = 227 * 1024 - 2048;
-    // the mode-a factor rows of the CTA's 128 columns, staged once per CTA when
-    // they fit beside at least two pipeline stages
+    // Shared memory: a double-buffered A ring (the producers stay one tile
+    // ahead), a TMA-fed B ring as deep as fits (up to 6) to hide the latency of
+    // T tiles, and, when that still leaves at least 3 B stages, the mode-a
+    // factor rows of the CTA's 128 columns (FP32 hi, BF16 lo), staged once.
     p.ua_parts = exact ? 2 : 1;
-    p.ua_stride = p.Ia_pad + 4;   // 16-byte skew between rows: fewer bank conflicts
-    const size_t ua_bytes = (size_t)p.ua_parts * 128 * p.ua_stride * sizeof(float);
-    p.ua_smem = (2 * stage + ua_bytes <= budget) ? 1 : 0;
-    const size_t avail = budget - (p.ua_smem ? ua_bytes : 0);
-    p.stages = (int)std::min<size_t>(4, avail / stage);
-    if (p.stages < 2) return fail(JKCALS_ERR_UNSUPPORTED, "tensor-core tile does not fit shared memory");
+    p.ua_stride = p.Ia_pad + 4;   // 16-byte skew between FP32 rows: fewer bank conflicts
+    p.stages_a = 2;
+    auto fit_b = [&](int ua) {
+      p.ua_smem = ua;
+      p.stages_b = 1;
+      while (p.stages_b < 6) {
+        ++p.stages_b;
+        if (tc::tc_smem_bytes(p) > kSmemOptin) {
+          --p.stages_b;
+          break;
+        }
+      }
+      return p.stages_b;
+    };
+    if (fit_b(1) < 3) fit_b(0);
+    if (p.stages_b < 2 || tc::tc_smem_bytes(p) > kSmemOptin)
+      return fail(JKCALS_ERR_UNSUPPORTED, "tensor-core tile does not fit shared memory");
     p.acc_cols = (int)round_up(p.BN, 32);
     p.tmem_cols = 32;
     while (p.tmem_cols < n_acc * p.acc_cols) p.tmem_cols *= 2;
@@ -210,37 +223,8 @@ jkcals_status make_tc_plan(jkcals_ctx* h) {
     if (exact) kchunk = std::min<int64_t>(kchunk, tc::kExactChainMax);   // exact chains
     p.kchunk = kchunk;
     p.splits = (int)((p.Jp + p.kchunk - 1) / p.kchunk);
+    p.nkt = ksteps;
     if (p.tiles_n > 65535 || p.splits > 65535) return fail(JKCALS_ERR_UNSUPPORTED, "grid too large");
-  }
-  return JKCALS_OK;
-}
-
-jkcals_status encode_tensor_maps(jkcals_ctx* h) {
-  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
-  if (encode == nullptr) {
-    void* fn = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
-    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || fn == nullptr)
-      return fail(JKCALS_ERR_CUDA, "cuTensorMapEncodeTiled entry point unavailable");
-    encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
-  }
-  const int prec = h->opt.precision;
-  const int eb = tc::form_elem_bytes(prec), bk = tc::form_bk(prec);
-  const CUtensorMapDataType dt = eb == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
-  for (int n = 0; n < h->N; ++n) {
-    const tc::TcPlan& p = h->tcplan[n];
-    const CUtensorMapSwizzle swz = p.row_bytes == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B;
-    for (int part = 0; part < 4; ++part) {
-      void* base = h->Tp[n][part < p.nsplit ? part : 0];
-      cuuint64_t gdim[2] = {(cuuint64_t)p.Jp, (cuuint64_t)h->dims[n]};
-      cuuint64_t gstride[1] = {(cuuint64_t)p.Jp * eb};
-      cuuint32_t box[2] = {(cuuint32_t)bk, (cuuint32_t)p.BN};
-      cuuint32_t estride[2] = {1, 1};
-      CUresult r = encode(&h->tmap[n][part], dt, 2, base, gdim, gstride, box, estride, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                          swz, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-      if (r != CUDA_SUCCESS) return fail(JKCALS_ERR_CUDA, "cuTensorMapEncodeTiled failed");
-    }
   }
   return JKCALS_OK;
 }
@@ -315,7 +299,10 @@ jkcals_status enqueue_mttkrp(jkcals_ctx* h, int n, double* const* U, float* cons
   a.BN = p.BN;
   a.tmem_cols = p.tmem_cols;
   a.acc_cols = p.acc_cols;
-  a.stages = p.stages;
+  a.nkt = p.nkt;
+  a.Tt = static_cast<const unsigned char*>(h->Tt[n]);
+  a.stages_a = p.stages_a;
+  a.stages_b = p.stages_b;
   a.Ia_pad = p.Ia_pad;
   a.UTa = UT[p.a_mode];
   a.UTa_lo = UTlo[p.a_mode];
@@ -336,7 +323,7 @@ jkcals_status enqueue_mttkrp(jkcals_ctx* h, int n, double* const* U, float* cons
   a.rowexp = h->rowexp[n];
   a.ua_smem = p.ua_smem;
   a.ua_stride = p.ua_stride;
-  JK_CUDA(h, tc::launch_mttkrp_tc(h->opt.precision, p, h->tmap[n], a, h->stream));
+  JK_CUDA(h, tc::launch_mttkrp_tc(h->opt.precision, p, a, h->stream));
   return JKCALS_OK;
 }
 
@@ -553,18 +540,13 @@ jkcals_status create_impl(jkcals_ctx* h, const void* T, int T_dtype, const int32
   dfree(h, slice);
   dfree(h, Tc);
 
-  // tensor-core forms: padded, precision-split unfoldings replace the FP64 ones
+  // tensor-core forms: padded, precision-split, pre-tiled unfoldings replace the FP64 ones
   if (h->tc) {
     JK_TRY(make_tc_plan(h));
-    const int eb = tc::form_elem_bytes(h->opt.precision);
     const int chunk = tc::form_chunk(h->opt.precision);
     for (int n = 0; n < N; ++n) {
       const tc::TcPlan& p = h->tcplan[n];
-      void* parts[4] = {nullptr, nullptr, nullptr, nullptr};
-      for (int q = 0; q < p.nsplit; ++q) {
-        JK_TRY(dalloc(h, &h->Tp[n][q], (size_t)h->dims[n] * p.Jp * eb));
-        parts[q] = h->Tp[n][q];
-      }
+      JK_TRY(dalloc(h, &h->Tt[n], (size_t)p.tiles_n * p.nkt * p.nsplit * p.BN * p.row_bytes));
       JK_TRY(dalloc_t(h, &h->rowexp[n], (size_t)h->dims[n]));
       JK_CUDA(h, tc::launch_row_exponent(h->Tn64[n], h->dims[n], h->J[n], h->rowexp[n], st));
       tc::UnfoldMap mp{};
@@ -582,8 +564,8 @@ jkcals_status create_impl(jkcals_ctx* h, const void* T, int T_dtype, const int32
           stride *= h->dims[k];
         }
       }
-      JK_CUDA(h, tc::launch_split_unfold(h->opt.precision, h->Tn64[n], h->dims[n], h->J[n],
-                                         h->dims[p.a_mode], p.Ia_pad, p.Jp, mp, h->rowexp[n], parts, st));
+      JK_CUDA(h, tc::launch_tile_unfold(h->opt.precision, h->Tn64[n], h->dims[n], h->J[n], h->dims[p.a_mode],
+                                        p.Ia_pad, p.Jp, mp, h->rowexp[n], p.BN, p.tiles_n, p.nkt, h->Tt[n], st));
       h->Ipad[n] = round_up(h->dims[n], chunk);
     }
     JK_CUDA(h, cudaStreamSynchronize(st));
@@ -598,7 +580,6 @@ jkcals_status create_impl(jkcals_ctx* h, const void* T, int T_dtype, const int32
         JK_CUDA(h, cudaMemsetAsync(h->UTlo[n], 0, sizeof(float) * h->C * h->Ipad[n], st));
       }
     }
-    JK_TRY(encode_tensor_maps(h));
     size_t smem = 0;
     for (int n = 0; n < N; ++n) smem = std::max(smem, tc::tc_smem_bytes(h->tcplan[n]));
     JK_CUDA(h, tc::prepare_mttkrp_tc(h->opt.precision, smem));

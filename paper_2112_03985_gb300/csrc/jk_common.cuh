@@ -13,7 +13,6 @@
 //   status    per-block status bits (JKCALS_BLOCK_*)
 #pragma once
 
-#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -64,7 +63,8 @@ struct TcPlan {
   int tiles_c;     // ceil(C / 128)
   int tiles_n;     // ceil(I_n / BN)
   int splits;      // split-K factor
-  int stages;      // pipeline depth
+  int stages_a;    // A ring depth (producer-built Khatri-Rao tiles)
+  int stages_b;    // B ring depth (TMA-loaded tiles of T_(n))
   int tmem_cols;   // power of two >= accumulators * acc_cols
   int acc_cols;    // TMEM column stride between accumulators
   int nsplit;      // operand parts of the form
@@ -73,9 +73,10 @@ struct TcPlan {
   int Ia_pad;      // its padded size
   int64_t Jp;      // padded columns of the unfolding
   int64_t kchunk;  // padded columns per split (multiple of the k-step)
+  int64_t nkt;     // k-steps per N tile: ceil(Jp / BK)
   int ua_smem;     // 1: the CTA keeps its 128 factor rows of mode a (hi, lo) in shared memory
-  int ua_stride;   // floats per staged row (Ia_pad plus a bank skew)
-  int ua_parts;    // staged copies: 1 (hi) or 2 (hi, lo)
+  int ua_stride;   // floats per staged FP32 row (Ia_pad plus a bank skew)
+  int ua_parts;    // staged copies: 1 (FP32 hi) or 2 (plus BF16 lo)
 };
 }  // namespace tc
 
@@ -144,13 +145,12 @@ struct jkcals_ctx {
 
   // tensor-core forms (precision != JKCALS_FP64)
   bool tc = false;
-  void* Tp[jk::kMaxModes][4] = {{nullptr}};  // split, padded unfoldings
+  void* Tt[jk::kMaxModes] = {nullptr};  // split, padded, pre-tiled unfoldings
   float* UT[jk::kMaxModes] = {nullptr};      // C x Ipad FP32 transposed factors
   float* gUT[jk::kMaxModes] = {nullptr};     // same, for the gradient's factor set
   float* UTlo[jk::kMaxModes] = {nullptr};    // exact-chain form: low parts, U = UT + UTlo
   float* gUTlo[jk::kMaxModes] = {nullptr};
   int64_t Ipad[jk::kMaxModes] = {0};
-  CUtensorMap tmap[jk::kMaxModes][4];
   jk::tc::TcPlan tcplan[jk::kMaxModes];
   float* cmax[jk::kMaxModes] = {nullptr};    // column maxima of UT (exact-chain grid)
   float* gcmax[jk::kMaxModes] = {nullptr};

@@ -8,18 +8,24 @@
 // submodels and its N dimension over the I_n rows of the mode (<= 256 per
 // tile), while the long contraction over J is split across CTAs (split-K).
 //
-// Roles inside one CTA (6 warps, one CTA per SM):
+// Roles inside one CTA (10 warps, one CTA per SM):
 //   warp 0     TMA producer: streams BN-row tiles of the (pre-split) unfolding
-//              T_(n) into shared memory (K-major, 128- or 64-byte swizzle).
+//              T_(n) into a ring of B stages.  The unfolding is stored pre-tiled
+//              in the exact shared-memory image of a stage (K-major, 128- or
+//              64-byte swizzle), so each stage is one contiguous bulk copy per
+//              part instead of BN short rows strided across T_(n).
 //   warp 1     owns TMEM; one lane issues tcgen05.mma (kind::tf32, or
 //              kind::f16 with BF16 operands) for every (A-part, B-part) pair
 //              of the precision form, accumulating in FP32 in TMEM.
-//   warps 2-5  build the 128 x BK tile of KRP_n^T in shared memory straight
-//              into the UMMA K-major swizzled layout: element (c, j) =
+//   warps 2-9  build the 128 x BK tile of KRP_n^T into a ring of A stages,
+//              straight in the UMMA K-major swizzled layout: element (c, j) =
 //              U_a^T(c, i_a(j)) * prod_{other k} U_k^T(c, i_k(j)), in FP32 from
-//              transposed FP32 copies of the factor multi-matrices, then split
-//              into the form's parts.  After the main loop they drain TMEM
-//              (tcgen05.ld 32x32b) and write this split's FP32 partial of Mbar_n.
+//              transposed FP32 copies of the factor multi-matrices (the rows of
+//              the fastest mode a are staged in shared memory once per CTA),
+//              then split into the form's parts.  After the main loop they drain
+//              TMEM (tcgen05.ld 32x32b) and write this split's partial of Mbar_n.
+// The A and B rings are separate: the small TMA-fed B ring gets as many stages
+// as fit, so T-tile latency is hidden even when the A ring is double-buffered.
 // The Khatri-Rao product never exists in global memory.
 //
 // Exact-chain form (JKCALS_EXACT_BF16): every operand value x of a row whose
@@ -29,14 +35,15 @@
 // level 1 (s0 t1 + s1 t0) are integer multiples of 1 and 2^-7 whose chain sums
 // stay below 2^24 units for chains of <= 1024 columns, so they accumulate
 // exactly in FP32 TMEM; levels 2-3 share a third accumulator whose truncation
-// is scaled by 2^-14.  The epilogue adds the three in FP64 and applies
-// 2^(E_c - 7) 2^(F_i - 7).
+// is scaled by 2^-14.  The Khatri-Rao entries themselves are formed as
+// unevaluated FP32 pairs (error-free FMA products of hi/lo factor copies).  The
+// epilogue adds the three accumulators with TwoSum into an FP32 pair and
+// applies 2^(E_c - 7) 2^(F_i - 7).
 //
-// Synchronisation: mbarriers per stage (T tile landed / KRP tile written /
-// stage consumed) plus one for the accumulator.  Every wait is bounded by a
-// wall-clock limit; on expiry the CTA records an error code, stops, waits
+// Synchronisation: mbarriers per A stage (tile written / consumed), per B stage
+// (tile landed / consumed) and one for the accumulator.  Every wait is bounded
+// by a wall-clock limit; on expiry the CTA records an error code, stops, waits
 // (bounded) for its own TMA copies and MMAs, frees its TMEM and returns.
-#include <cuda.h>
 #include <cuda_bf16.h>
 
 #include "jk_common.cuh"
@@ -53,7 +60,7 @@ constexpr int kProducerWarps = 8;                    // two per scheduler: hides
 constexpr int kThreads = 32 * (2 + kProducerWarps);  // + the TMA warp and the MMA warp
 constexpr int kProducerWarp0 = 2;
 constexpr int kRowsPerWarp = 128 / kProducerWarps;   // rows of the A tile per producer warp
-constexpr int kRowsM = 128;   // MMA M
+constexpr int kRowsM = 128;                          // MMA M
 
 // UMMA shared-memory descriptor: K-major operand, ROW-byte swizzle (128 -> 2,
 // 64 -> 4), 8-row groups 8*ROW bytes apart (SBO), version 1 (tcgen05).
@@ -87,8 +94,14 @@ __device__ __forceinline__ int bound_exponent(double b) {
   return e < -110 ? -110 : (e > 110 ? 110 : e);
 }
 
-// Split one FP32 value into the form's parts (returned as FP32 values that the
-// part's storage type represents exactly).
+// BF16 bit patterns of values that BF16 represents exactly (the slices and
+// splits): the upper 16 bits of the FP32 pattern; two per 32-bit word.
+__device__ __forceinline__ uint32_t pack_bf16_exact(float lo, float hi) {
+  return __byte_perm(__float_as_uint(lo), __float_as_uint(hi), 0x7632);
+}
+
+// Split one FP32 value (plus a low part for the exact-chain form) into the
+// form's parts, returned as FP32 values that the part's storage represents exactly.
 template <class Cfg>
 __device__ __forceinline__ void split_value(float v, float vl, float scale, float (&p)[4]) {
   if constexpr (Cfg::exact) {
@@ -127,9 +140,7 @@ __device__ __forceinline__ void split_value(float v, float vl, float scale, floa
 
 template <class Cfg>
 __global__ void __launch_bounds__(kThreads, 1)
-    mttkrp_tc_kernel(const __grid_constant__ CUtensorMap tm0, const __grid_constant__ CUtensorMap tm1,
-                     const __grid_constant__ CUtensorMap tm2, const __grid_constant__ CUtensorMap tm3,
-                     const TcArgs a) {
+    mttkrp_tc_kernel(const TcArgs a) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem =
       reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -143,18 +154,24 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t a_bytes = kRowsM * ROW;
   const uint32_t b_bytes = (uint32_t)a.BN * ROW;
-  const uint32_t stage_bytes = NS * (a_bytes + b_bytes);
-  const int STAGES = a.stages;
-  // staged mode-a factor rows (hi, then lo for the exact-chain form) follow the stages
-  float* ua_hi = reinterpret_cast<float*>(smem + (size_t)STAGES * stage_bytes);
-  const size_t ua_floats = a.ua_smem ? (size_t)kRowsM * a.ua_stride : 0;
-  float* ua_lo = ua_hi + ua_floats;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(ua_hi + ua_floats * (Cfg::exact ? 2 : 1));
+  const uint32_t a_stage = NS * a_bytes, b_stage = NS * b_bytes;
+  const int SA = a.stages_a, SB = a.stages_b;
+  // layout: A ring | B ring | staged mode-a rows (FP32 hi, BF16 lo) | barriers
+  unsigned char* a_ring = smem;
+  unsigned char* b_ring = smem + (size_t)SA * a_stage;
+  float* ua_hi = reinterpret_cast<float*>(b_ring + (size_t)SB * b_stage);
+  // staged rows: FP32 with a 16-byte skew (ua_stride floats), BF16 low parts
+  // densely (Ia_pad elements: a multiple of 8, so rows stay 16-byte aligned)
+  const size_t ua_n = a.ua_smem ? (size_t)kRowsM * a.ua_stride : 0;
+  const size_t ua_ln = (a.ua_smem && Cfg::exact) ? (size_t)kRowsM * a.Ia_pad : 0;
+  __nv_bfloat16* ua_lo = reinterpret_cast<__nv_bfloat16*>(ua_hi + ua_n);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(ua_lo + ua_ln);
   uint64_t* full_a = bars;
-  uint64_t* full_b = bars + STAGES;
-  uint64_t* empty = bars + 2 * STAGES;
-  uint64_t* accum = bars + 3 * STAGES;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 3 * STAGES + 1);
+  uint64_t* empty_a = bars + SA;
+  uint64_t* full_b = bars + 2 * SA;
+  uint64_t* empty_b = bars + 2 * SA + SB;
+  uint64_t* accum = bars + 2 * SA + 2 * SB;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accum + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
   const int c0 = blockIdx.x * kRowsM;
@@ -165,18 +182,17 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int nk = (je > jb) ? (int)((je - jb + BK - 1) / BK) : 0;
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < STAGES; ++s) {
-      mbar_init(&full_a[s], 32 * kProducerWarps);
+    for (int s = 0; s < SA; ++s) {
+      mbar_init(&full_a[s], kProducerWarps);   // one arrival per producer warp
+      mbar_init(&empty_a[s], 1);
+    }
+    for (int s = 0; s < SB; ++s) {
       mbar_init(&full_b[s], 1);
-      mbar_init(&empty[s], 1);
+      mbar_init(&empty_b[s], 1);
     }
     mbar_init(accum, 1);
     *abort_flag = 0;
     fence_barrier_init();
-    tma_prefetch_desc(&tm0);
-    if (NS > 1) tma_prefetch_desc(&tm1);
-    if (NS > 2) tma_prefetch_desc(&tm2);
-    if (NS > 3) tma_prefetch_desc(&tm3);
   }
   if (warp == 1) tmem_alloc(tmem_slot, (uint32_t)a.tmem_cols);
   tc_fence_before();
@@ -184,57 +200,61 @@ __global__ void __launch_bounds__(kThreads, 1)
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
 
-  auto a_tile = [&](int s, int p) -> unsigned char* { return smem + (size_t)s * stage_bytes + p * a_bytes; };
-  auto b_tile = [&](int s, int p) -> unsigned char* {
-    return smem + (size_t)s * stage_bytes + NS * a_bytes + p * b_bytes;
-  };
-
   if (warp == 0) {
     // ---------------- TMA producer: tiles of T_(n) ------------------------------
     if (lane == 0) {
       int issued = 0;
+      // this CTA's first stage image: N tile blockIdx.y, k-step jb / BK
+      const unsigned char* src = a.Tt + ((int64_t)blockIdx.y * a.nkt + jb / BK) * (int64_t)b_stage;
       for (int it = 0; it < nk; ++it) {
-        const int s = it % STAGES;
-        const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
-        if (!wait_bounded(&empty[s], ph ^ 1u, abort_flag, a.err, 1)) break;
-        mbar_arrive_expect_tx(&full_b[s], NS * b_bytes);
-        const int x = (int)(jb + (int64_t)it * BK);
-        tma_load_2d(b_tile(s, 0), &tm0, &full_b[s], x, n0);
-        if (NS > 1) tma_load_2d(b_tile(s, 1), &tm1, &full_b[s], x, n0);
-        if (NS > 2) tma_load_2d(b_tile(s, 2), &tm2, &full_b[s], x, n0);
-        if (NS > 3) tma_load_2d(b_tile(s, 3), &tm3, &full_b[s], x, n0);
+        const int s = it % SB;
+        const uint32_t ph = (uint32_t)(it / SB) & 1u;
+        if (!wait_bounded(&empty_b[s], ph ^ 1u, abort_flag, a.err, 1)) break;
+        mbar_arrive_expect_tx(&full_b[s], b_stage);
+        unsigned char* dst = b_ring + (size_t)s * b_stage;
+#pragma unroll
+        for (int p = 0; p < NS; ++p) bulk_load(dst + p * b_bytes, src + p * b_bytes, b_bytes, &full_b[s]);
+        src += b_stage;
         issued = it + 1;
       }
       if (*abort_flag) {
         // let every copy this thread started land before the CTA exits
-        for (int it = (issued > STAGES ? issued - STAGES : 0); it < issued; ++it)
-          wait_drain(&full_b[it % STAGES], (uint32_t)(it / STAGES) & 1u);
+        for (int it = (issued > SB ? issued - SB : 0); it < issued; ++it)
+          wait_drain(&full_b[it % SB], (uint32_t)(it / SB) & 1u);
       }
     }
   } else if (warp == 1) {
     // ---------------- MMA issuer --------------------------------------------------
     if (lane == 0) {
       const uint32_t idesc = make_idesc(Cfg::fmt, kRowsM, (uint32_t)a.BN);
+      // The descriptor's start-address field is (address >> 4) in its low 14
+      // bits, so every operand descriptor is the region's base descriptor plus
+      // (byte offset >> 4): one add per MMA instead of rebuilding it.
+      const uint64_t adesc0 = smem_desc<ROW>(smem_u32(a_ring));
+      const uint64_t bdesc0 = smem_desc<ROW>(smem_u32(b_ring));
+      const uint32_t tmem_acc1 = tmem + (uint32_t)a.acc_cols, tmem_acc2 = tmem + 2u * (uint32_t)a.acc_cols;
       bool ok = true;
       for (int it = 0; it < nk && ok; ++it) {
-        const int s = it % STAGES;
-        const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
-        ok = wait_bounded(&full_b[s], ph, abort_flag, a.err, 2) &&
-             wait_bounded(&full_a[s], ph, abort_flag, a.err, 3);
+        const int sa = it % SA, sb = it % SB;
+        ok = wait_bounded(&full_b[sb], (uint32_t)(it / SB) & 1u, abort_flag, a.err, 2) &&
+             wait_bounded(&full_a[sa], (uint32_t)(it / SA) & 1u, abort_flag, a.err, 3);
         if (!ok) break;
         tc_fence_after();
+        const uint64_t ad0 = adesc0 + (uint64_t)(((uint32_t)sa * a_stage) >> 4);
+        const uint64_t bd0 = bdesc0 + (uint64_t)(((uint32_t)sb * b_stage) >> 4);
 #pragma unroll
         for (int kk = 0; kk < ROW / 32; ++kk) {
 #pragma unroll
           for (int q = 0; q < Cfg::npass; ++q) {
-            const uint64_t ad = smem_desc<ROW>(smem_u32(a_tile(s, Cfg::pass_a(q))) + kk * 32);
-            const uint64_t bd = smem_desc<ROW>(smem_u32(b_tile(s, Cfg::pass_b(q))) + kk * 32);
-            const uint32_t d = tmem + (uint32_t)(Cfg::pass_acc(q) * a.acc_cols);
+            const uint64_t ad = ad0 + (uint64_t)((Cfg::pass_a(q) * a_bytes + kk * 32) >> 4);
+            const uint64_t bd = bd0 + (uint64_t)((Cfg::pass_b(q) * b_bytes + kk * 32) >> 4);
+            const uint32_t d = Cfg::pass_acc(q) == 0 ? tmem : (Cfg::pass_acc(q) == 1 ? tmem_acc1 : tmem_acc2);
             const bool first = (it == 0 && kk == 0 && Cfg::first_of_acc(q));
             tc_mma<Cfg::kind>(d, ad, bd, idesc, first ? 0u : 1u);
           }
         }
-        tc_commit(&empty[s]);
+        tc_commit(&empty_a[sa]);
+        tc_commit(&empty_b[sb]);
       }
       // Always signal the accumulator: its phase completes once every MMA issued
       // above has finished, so on an abort this lane drains them before TMEM is freed.
@@ -242,22 +262,21 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (!ok) wait_drain(accum, 0);
     }
   } else {
-    // ---------------- Khatri-Rao producers (warps 2..) -------------------------------
+    // ---------------- Khatri-Rao producers (warps 2..9) ------------------------------
     const int pw = warp - kProducerWarp0;   // 0..kProducerWarps-1
     const int rg = lane / CPR;              // row within a group of RPI rows
     const int q = lane % CPR;               // 16-byte chunk within the row
-    // per-row constants, hoisted out of the k loop: validity, global row
-    // pointers of the factor copies, the swizzled shared-memory offset and the
-    // exact-chain scale 2^(7 - E_c)
+    // per-row constants, hoisted out of the k loop
     bool cval[ROWS_PER_THREAD];
     float rscale[ROWS_PER_THREAD];
-    uint32_t soff[ROWS_PER_THREAD];
-    const float* ra[ROWS_PER_THREAD];
+    uint32_t soff[ROWS_PER_THREAD];                      // swizzled offset in an A tile
+    const float* ra[ROWS_PER_THREAD];                    // global rows of UTa (unstaged path)
     const float* ral[ROWS_PER_THREAD];
     const float* rq0[ROWS_PER_THREAD];
     const float* rq0l[ROWS_PER_THREAD];
     const float* rq1[ROWS_PER_THREAD];
     const float* rq1l[ROWS_PER_THREAD];
+    uint32_t ua_row[ROWS_PER_THREAD], ua_rowl[ROWS_PER_THREAD];   // staged rows (shared addresses)
 #pragma unroll
     for (int rr = 0; rr < ROWS_PER_THREAD; ++rr) {
       const int m = pw * kRowsPerWarp + rr * RPI + rg;   // row of the A tile = column c0 + m
@@ -272,6 +291,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       rq0l[rr] = (Cfg::exact && a.nq > 0) ? a.UTq_lo[0] + (int64_t)cc * a.qpad[0] : nullptr;
       rq1[rr] = a.nq > 1 ? a.UTq[1] + (int64_t)cc * a.qpad[1] : nullptr;
       rq1l[rr] = (Cfg::exact && a.nq > 1) ? a.UTq_lo[1] + (int64_t)cc * a.qpad[1] : nullptr;
+      ua_row[rr] = smem_u32(ua_hi + (size_t)m * a.ua_stride);
+      ua_rowl[rr] = smem_u32(ua_lo + (size_t)m * a.Ia_pad);
       rscale[rr] = 1.f;
       if constexpr (Cfg::exact) {
         if (cval[rr]) {
@@ -284,28 +305,47 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
     }
     if (a.ua_smem) {
-      // stage the CTA's 128 factor rows of mode a once; the k loop then reads
-      // them from shared memory instead of L2
+      // stage the CTA's 128 factor rows of mode a once (FP32 hi; BF16 lo for
+      // the exact-chain form, which keeps the pair to ~2^-32): the k loop then
+      // reads them from shared memory instead of L2
       const int ptid = threadIdx.x - 32 * kProducerWarp0;
       const int n4 = a.Ia_pad / 4;
-      for (int idx = ptid; idx < kRowsM * n4; idx += 32 * kProducerWarps) {
-        const int row = idx / n4, col = (idx - row * n4) * 4;
-        const int c = c0 + row;
-        float4 hv = make_float4(0.f, 0.f, 0.f, 0.f), lv = hv;
-        if (c < a.C) {
-          hv = __ldg(reinterpret_cast<const float4*>(a.UTa + (int64_t)c * a.Ia_pad + col));
-          if constexpr (Cfg::exact) lv = __ldg(reinterpret_cast<const float4*>(a.UTa_lo + (int64_t)c * a.Ia_pad + col));
+      const int total = kRowsM * n4;
+      constexpr int kU = 4;   // loads in flight per thread
+      for (int idx0 = ptid; idx0 < total; idx0 += kU * 32 * kProducerWarps) {
+        float4 hv[kU], lv[kU];
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+          const int idx = idx0 + u * 32 * kProducerWarps;
+          const int row = idx / n4, col = (idx - row * n4) * 4;
+          const int c = c0 + row;
+          hv[u] = lv[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (idx < total && c < a.C) {
+            hv[u] = __ldg(reinterpret_cast<const float4*>(a.UTa + (int64_t)c * a.Ia_pad + col));
+            if constexpr (Cfg::exact)
+              lv[u] = __ldg(reinterpret_cast<const float4*>(a.UTa_lo + (int64_t)c * a.Ia_pad + col));
+          }
         }
-        *reinterpret_cast<float4*>(ua_hi + (size_t)row * a.ua_stride + col) = hv;
-        if constexpr (Cfg::exact) *reinterpret_cast<float4*>(ua_lo + (size_t)row * a.ua_stride + col) = lv;
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+          const int idx = idx0 + u * 32 * kProducerWarps;
+          if (idx < total) {
+            const int row = idx / n4, col = (idx - row * n4) * 4;
+            sts128(smem_u32(ua_hi + (size_t)row * a.ua_stride + col),
+                   make_uint4(__float_as_uint(hv[u].x), __float_as_uint(hv[u].y), __float_as_uint(hv[u].z),
+                              __float_as_uint(hv[u].w)));
+            if constexpr (Cfg::exact) {
+              const __nv_bfloat162 l01 = __floats2bfloat162_rn(lv[u].x, lv[u].y);
+              const __nv_bfloat162 l23 = __floats2bfloat162_rn(lv[u].z, lv[u].w);
+              uint2 pk;
+              pk.x = *reinterpret_cast<const uint32_t*>(&l01);
+              pk.y = *reinterpret_cast<const uint32_t*>(&l23);
+              *reinterpret_cast<uint2*>(ua_lo + (size_t)row * a.Ia_pad + col) = pk;
+            }
+          }
+        }
       }
       asm volatile("bar.sync 1, %0;" ::"r"(32 * kProducerWarps) : "memory");   // producer warps only
-#pragma unroll
-      for (int rr = 0; rr < ROWS_PER_THREAD; ++rr) {
-        const int m = pw * kRowsPerWarp + rr * RPI + rg;
-        ra[rr] = ua_hi + (size_t)m * a.ua_stride;
-        ral[rr] = ua_lo + (size_t)m * a.ua_stride;
-      }
     }
     float qhc[ROWS_PER_THREAD], qlc[ROWS_PER_THREAD];   // cached remaining-mode products
     bool qstale = true;
@@ -329,11 +369,16 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
       }
     }
+    const uint32_t a_ring_s = smem_u32(a_ring);
     bool ok = true;
     for (int it = 0; it < nk && ok; ++it) {
-      const int s = it % STAGES;
-      const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
-      if (!wait_bounded(&empty[s], ph ^ 1u, abort_flag, a.err, 4)) {
+      const int s = it % SA;
+      // one lane per warp polls the barrier; __syncwarp orders the others after it
+      bool got = true;
+      if (lane == 0) got = wait_bounded(&empty_a[s], ((uint32_t)(it / SA) & 1u) ^ 1u, abort_flag, a.err, 4);
+      got = __shfl_sync(0xffffffffu, got, 0);
+      __syncwarp();
+      if (!got) {
         ok = false;
         break;
       }
@@ -377,39 +422,68 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         qstale = false;
       }
+      const uint32_t a_tile_s = a_ring_s + (uint32_t)s * a_stage;
 #pragma unroll
       for (int rr = 0; rr < ROWS_PER_THREAD; ++rr) {
         float v[CHUNK], vl[CHUNK];
 #pragma unroll
         for (int e = 0; e < CHUNK; ++e) v[e] = vl[e] = 0.f;
         if (jvalid && cval[rr]) {
+          const float qh = qhc[rr];
           if constexpr (!Cfg::exact) {
-            const float qv = qhc[rr];
             const float4* src = reinterpret_cast<const float4*>(ra[rr] + ia);
 #pragma unroll
             for (int e4 = 0; e4 < CHUNK / 4; ++e4) {
-              const float4 u = src[e4];   // generic load: shared (staged rows) or global
-              v[4 * e4 + 0] = u.x * qv;
-              v[4 * e4 + 1] = u.y * qv;
-              v[4 * e4 + 2] = u.z * qv;
-              v[4 * e4 + 3] = u.w * qv;
+              const float4 u = a.ua_smem ? lds128(ua_row[rr] + (uint32_t)(ia + 4 * e4) * 4u) : __ldg(src + e4);
+              v[4 * e4 + 0] = u.x * qh;
+              v[4 * e4 + 1] = u.y * qh;
+              v[4 * e4 + 2] = u.z * qh;
+              v[4 * e4 + 3] = u.w * qh;
             }
           } else {
             // Khatri-Rao entry as an unevaluated pair (v + vl) from hi/lo factor
-            // copies: error-free products (FMA) keep it to ~2^-44 relative
-            const float qh = qhc[rr], ql = qlc[rr];
-            const float4* src = reinterpret_cast<const float4*>(ra[rr] + ia);
-            const float4* srcl = reinterpret_cast<const float4*>(ral[rr] + ia);
+            // copies: error-free products (FMA) keep it far below FP32 rounding
+            const float ql = qlc[rr];
+            float uh[CHUNK], ul[CHUNK];
+            if (a.ua_smem) {
 #pragma unroll
-            for (int e4 = 0; e4 < CHUNK / 4; ++e4) {
-              const float4 u = src[e4], ul = srcl[e4];   // generic loads: shared or global
-              const float uh4[4] = {u.x, u.y, u.z, u.w}, ul4[4] = {ul.x, ul.y, ul.z, ul.w};
+              for (int e4 = 0; e4 < CHUNK / 4; ++e4) {
+                const float4 u = lds128(ua_row[rr] + (uint32_t)(ia + 4 * e4) * 4u);
+                uh[4 * e4 + 0] = u.x;
+                uh[4 * e4 + 1] = u.y;
+                uh[4 * e4 + 2] = u.z;
+                uh[4 * e4 + 3] = u.w;
+              }
+              // CHUNK (8) BF16 low parts in one 16-byte load
+              const float4 lraw = lds128(ua_rowl[rr] + (uint32_t)ia * 2u);
+              const uint32_t w4[4] = {__float_as_uint(lraw.x), __float_as_uint(lraw.y), __float_as_uint(lraw.z),
+                                      __float_as_uint(lraw.w)};
 #pragma unroll
               for (int k = 0; k < 4; ++k) {
-                const float p = __fmul_rn(uh4[k], qh);
-                v[4 * e4 + k] = p;
-                vl[4 * e4 + k] = __fadd_rn(__fmaf_rn(uh4[k], qh, -p), __fmaf_rn(uh4[k], ql, __fmul_rn(ul4[k], qh)));
+                ul[2 * k] = __uint_as_float(w4[k] << 16);
+                ul[2 * k + 1] = __uint_as_float(w4[k] & 0xffff0000u);
               }
+            } else {
+              const float4* src = reinterpret_cast<const float4*>(ra[rr] + ia);
+              const float4* srcl = reinterpret_cast<const float4*>(ral[rr] + ia);
+#pragma unroll
+              for (int e4 = 0; e4 < CHUNK / 4; ++e4) {
+                const float4 u = __ldg(src + e4), l = __ldg(srcl + e4);
+                uh[4 * e4 + 0] = u.x;
+                uh[4 * e4 + 1] = u.y;
+                uh[4 * e4 + 2] = u.z;
+                uh[4 * e4 + 3] = u.w;
+                ul[4 * e4 + 0] = l.x;
+                ul[4 * e4 + 1] = l.y;
+                ul[4 * e4 + 2] = l.z;
+                ul[4 * e4 + 3] = l.w;
+              }
+            }
+#pragma unroll
+            for (int k = 0; k < CHUNK; ++k) {
+              const float p = __fmul_rn(uh[k], qh);
+              v[k] = p;
+              vl[k] = __fadd_rn(__fmaf_rn(uh[k], qh, -p), __fmaf_rn(uh[k], ql, __fmul_rn(ul[k], qh)));
             }
           }
         }
@@ -430,18 +504,17 @@ __global__ void __launch_bounds__(kThreads, 1)
             w.z = __float_as_uint(parts[p][2]);
             w.w = __float_as_uint(parts[p][3]);
           } else {
-            __nv_bfloat162 b0 = __floats2bfloat162_rn(parts[p][0], parts[p][1]);
-            __nv_bfloat162 b1 = __floats2bfloat162_rn(parts[p][2], parts[p][3]);
-            __nv_bfloat162 b2 = __floats2bfloat162_rn(parts[p][4], parts[p][5]);
-            __nv_bfloat162 b3 = __floats2bfloat162_rn(parts[p][6], parts[p][7]);
-            w.x = *reinterpret_cast<uint32_t*>(&b0);
-            w.y = *reinterpret_cast<uint32_t*>(&b1);
-            w.z = *reinterpret_cast<uint32_t*>(&b2);
-            w.w = *reinterpret_cast<uint32_t*>(&b3);
+            w.x = pack_bf16_exact(parts[p][0], parts[p][1]);
+            w.y = pack_bf16_exact(parts[p][2], parts[p][3]);
+            w.z = pack_bf16_exact(parts[p][4], parts[p][5]);
+            w.w = pack_bf16_exact(parts[p][6], parts[p][7]);
           }
-          *reinterpret_cast<uint4*>(a_tile(s, p) + soff[rr]) = w;
+          sts128(a_tile_s + (uint32_t)p * a_bytes + soff[rr], w);
         }
       }
+      fence_async_shared();   // each writer: generic-proxy stores -> visible to the MMA
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&full_a[s]);
       // advance this thread's column by BK: carry i_a into the remaining modes
       jcur += BK;
       ia += BK;
@@ -456,15 +529,13 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
         }
       }
-      fence_async_shared();
-      mbar_arrive(&full_a[s]);
     }
 
-    // ---------------- epilogue: TMEM -> FP32 partial of Mbar_n --------------------
+    // ---------------- epilogue: TMEM -> partial of Mbar_n ----------------------------
     bool have = ok && nk > 0 && wait_bounded(accum, 0, abort_flag, a.err, 5);
     have = __all_sync(0xffffffffu, have);   // tcgen05.ld is warp-collective
     tc_fence_after();
-    const int quarter = warp & 3;             // TMEM lanes 32*quarter .. +31
+    const int quarter = warp & 3;                    // TMEM lanes 32*quarter .. +31
     const int half = (warp - kProducerWarp0) >> 2;   // two warps per lane quarter split the columns
     const int m = quarter * 32 + lane;
     const int c = c0 + m;
@@ -512,7 +583,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         // level 0 and level 1 are exact; add the three as an unevaluated FP32 pair
         // (hi, lo) with error-free TwoSum steps, scale by 2^(E_c + F_i - 14) and
-        // store the pair; the consumer adds hi + lo in FP64
+        // store the pair; the consumer adds hi + lo
         float2* out2 = reinterpret_cast<float2*>(a.part) + (int64_t)blockIdx.z * a.I * a.C;
 #pragma unroll
         for (int r = 0; r < 32; ++r) {
@@ -604,10 +675,10 @@ cudaError_t set_smem_cfg(size_t smem) {
 }
 
 template <class Cfg>
-cudaError_t launch_cfg(const TcPlan& p, const CUtensorMap* maps, const TcArgs& a, cudaStream_t s) {
+cudaError_t launch_cfg(const TcPlan& p, const TcArgs& a, cudaStream_t s) {
   const size_t smem = tc_smem_bytes(p);
   dim3 grid((unsigned)p.tiles_c, (unsigned)p.tiles_n, (unsigned)p.splits);
-  mttkrp_tc_kernel<Cfg><<<grid, kThreads, smem, s>>>(maps[0], maps[1], maps[2], maps[3], a);
+  mttkrp_tc_kernel<Cfg><<<grid, kThreads, smem, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -639,11 +710,18 @@ int form_passes(int precision) {
   }
 }
 
+size_t tc_ua_bytes(const TcPlan& p) {
+  if (!p.ua_smem) return 0;
+  return (size_t)kRowsM * p.ua_stride * sizeof(float) +
+         (p.ua_parts > 1 ? (size_t)kRowsM * p.Ia_pad * sizeof(__nv_bfloat16) : 0);
+}
+
 size_t tc_smem_bytes(const TcPlan& p) {
   const size_t row = (size_t)p.row_bytes;
-  const size_t stage = (size_t)p.nsplit * (kRowsM * row + (size_t)p.BN * row);
-  const size_t ua = p.ua_smem ? (size_t)p.ua_parts * kRowsM * p.ua_stride * sizeof(float) : 0;
-  return 1024 /*alignment slack*/ + (size_t)p.stages * stage + ua + (3 * p.stages + 1) * 8 + 16;
+  const size_t a_stage = (size_t)p.nsplit * kRowsM * row;
+  const size_t b_stage = (size_t)p.nsplit * p.BN * row;
+  return 1024 /*alignment slack*/ + (size_t)p.stages_a * a_stage + (size_t)p.stages_b * b_stage + tc_ua_bytes(p) +
+         (2 * p.stages_a + 2 * p.stages_b + 1) * 8 + 16;
 }
 
 cudaError_t prepare_mttkrp_tc(int precision, size_t max_smem) {
@@ -657,14 +735,13 @@ cudaError_t prepare_mttkrp_tc(int precision, size_t max_smem) {
   }
 }
 
-cudaError_t launch_mttkrp_tc(int precision, const TcPlan& p, const CUtensorMap* maps, const TcArgs& a,
-                             cudaStream_t s) {
+cudaError_t launch_mttkrp_tc(int precision, const TcPlan& p, const TcArgs& a, cudaStream_t s) {
   switch (precision) {
-    case JKCALS_TF32: return launch_cfg<CfgTF32>(p, maps, a, s);
-    case JKCALS_3XTF32: return launch_cfg<Cfg3xTF32>(p, maps, a, s);
-    case JKCALS_BF16: return launch_cfg<CfgBF16>(p, maps, a, s);
-    case JKCALS_SPLIT_BF16: return launch_cfg<CfgBF16x3>(p, maps, a, s);
-    case JKCALS_EXACT_BF16: return launch_cfg<CfgExact>(p, maps, a, s);
+    case JKCALS_TF32: return launch_cfg<CfgTF32>(p, a, s);
+    case JKCALS_3XTF32: return launch_cfg<Cfg3xTF32>(p, a, s);
+    case JKCALS_BF16: return launch_cfg<CfgBF16>(p, a, s);
+    case JKCALS_SPLIT_BF16: return launch_cfg<CfgBF16x3>(p, a, s);
+    case JKCALS_EXACT_BF16: return launch_cfg<CfgExact>(p, a, s);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -1,18 +1,20 @@
 // Declarations of the tensor-core (tcgen05) forms of the concurrent MTTKRP.
 //
 // Operand layouts in HBM (one handle, forms TF32 / 3xTF32 / BF16 / BF16x3 / exact BF16):
-//   Tp[n][p]  part p of the split mode-n unfolding, I_n x Jp_n row-major (FP32
-//             holding TF32 values, or BF16), Jp_n = Ia_pad * prod(remaining dims):
-//             the fastest other mode a is padded with zeros to Ia_pad (a multiple
-//             of the 16-byte chunk) so that a chunk never straddles two rows of
-//             the remaining modes.
+//   Tt[n]     the split mode-n unfolding, pre-tiled into the exact shared-memory
+//             image of the MMA's B operand: for N tile t (BN rows of I_n, zero
+//             padded) and k-step s (BK columns of the padded unfolding), the
+//             nsplit parts follow each other, each BN rows x ROW bytes, K-major,
+//             in the ROW-byte swizzle (128 or 64).  One stage of the pipeline is
+//             then one contiguous bulk copy.  Columns jp = ia + Ia_pad * o: ia
+//             indexes the fastest other mode a, padded with zeros to Ia_pad (a
+//             multiple of the 16-byte chunk) so that a chunk never straddles two
+//             rows of the remaining modes; o runs mixed-radix over the others.
 //   UT[n]     FP32 transposed copy of Ubar^(n): C x I_pad_n (zero padded), written
 //             by the update kernel after every mode update.
 //   cmax[n]   C floats, max_i |UT[n][c][i]| (exact-chain form: per-row grid of KRP^T).
 //   rowexp[n] I_n ints, F_i with max_j |T_(n)(i, j)| < 2^F_i (exact-chain form).
 #pragma once
-
-#include <cuda.h>
 
 #include "jk_common.cuh"
 
@@ -28,9 +30,12 @@ constexpr int kSliceBits = 7;
 
 struct TcArgs {
   int64_t I, Jp, kchunk;
-  int C, BN, tmem_cols, stages;
+  int C, BN, tmem_cols;
+  int stages_a, stages_b;          // A ring (Khatri-Rao tiles) and B ring (T tiles) depths
   int acc_cols;                    // TMEM column stride between accumulators
   int Ia_pad;
+  int64_t nkt;                     // k-steps per N tile in Tt
+  const unsigned char* Tt;         // pre-tiled unfolding (layout above)
   int nq;                          // remaining other modes (N - 2)
   int qdims[kMaxModes - 2];
   int qpad[kMaxModes - 2];
@@ -45,7 +50,7 @@ struct TcArgs {
   const float* cmax_q[kMaxModes - 2];
   const int* rowexp;               // I_n: F_i of this mode's unfolding
   int ua_smem;                     // stage the 128 rows of UTa (and UTa_lo) in shared memory
-  int ua_stride;                   // floats per staged row
+  int ua_stride;                   // floats per staged FP32 row (BF16 low rows: Ia_pad elements)
 };
 
 int form_nsplit(int precision);
@@ -57,8 +62,7 @@ int form_passes(int precision);
 size_t tc_smem_bytes(const TcPlan& p);
 // Raise the kernel's dynamic shared-memory limit (call once, outside stream capture).
 cudaError_t prepare_mttkrp_tc(int precision, size_t max_smem);
-cudaError_t launch_mttkrp_tc(int precision, const TcPlan& p, const CUtensorMap* maps, const TcArgs& a,
-                             cudaStream_t s);
+cudaError_t launch_mttkrp_tc(int precision, const TcPlan& p, const TcArgs& a, cudaStream_t s);
 
 // create-time conversions (jk_tc_prep.cu)
 // rowexp[i] = smallest F with max_j |Tn64(i, j)| < 2^F (0 for an all-zero row)
@@ -71,10 +75,12 @@ struct UnfoldMap {
   int64_t qd[kMaxModes - 2];
   int64_t qs[kMaxModes - 2];
 };
-// split (and for the exact form slice, using rowexp) the padded unfolding into its parts
-cudaError_t launch_split_unfold(int precision, const double* Tn64, int64_t I, int64_t J, int64_t Ia,
-                                int64_t Ia_pad, int64_t Jp, const UnfoldMap& mp, const int* rowexp,
-                                void* const* parts, cudaStream_t s);
+// Split (and for the exact form slice, using rowexp) the padded unfolding into
+// its parts and write them pre-tiled (layout above) into Tt, whose size is
+// tiles_n * nkt * nsplit * BN * row_bytes bytes.
+cudaError_t launch_tile_unfold(int precision, const double* Tn64, int64_t I, int64_t J, int64_t Ia, int64_t Ia_pad,
+                               int64_t Jp, const UnfoldMap& mp, const int* rowexp, int BN, int tiles_n, int64_t nkt,
+                               void* Tt, cudaStream_t s);
 // UT[c][i] = fl32(U[i][c]); if UT_lo != NULL also UT_lo[c][i] = fl32(U[i][c] - UT[c][i])
 cudaError_t launch_factor_to_ut(const double* U, int64_t I, int C, float* UT, float* UT_lo, int64_t I_pad,
                                 cudaStream_t s);

@@ -34,38 +34,58 @@ __global__ void row_exponent_kernel(const double* __restrict__ Tn, int64_t J, in
   }
 }
 
-// parts[p][i * Jp + jp] = part p of T_(n)(i, j) with jp = ia + Ia_pad * o: ia is
-// the index of the fastest mode a, o runs mixed-radix over the remaining modes
-// in increasing order, and j is the Eq. kolda_mapping column of those indices;
-// zero where ia >= Ia.  Splits are taken from the FP64 value.
+// Byte offset of element (r, col) of one part tile (BN rows x ROW bytes,
+// K-major) in the ROW-byte swizzle of the MMA's shared-memory operands: rows
+// in groups of 8 (8 * ROW bytes apart), the 16-byte chunk index XORed with
+// the row (ROW = 128) or with row / 2 (ROW = 64).
+__device__ __forceinline__ int64_t swizzled_offset(int r, int cb, int row_bytes) {
+  const int sw = row_bytes == 128 ? (r & 7) : ((r >> 1) & 3);
+  return (int64_t)(r >> 3) * (8 * row_bytes) + (int64_t)(r & 7) * row_bytes + (((cb >> 4) ^ sw) << 4) + (cb & 15);
+}
+
+// Tt holds, for N tile t and k-step s, the parts of rows t*BN .. t*BN+BN-1 and
+// padded columns s*BK .. s*BK+BK-1 (see jk_tc.cuh).  Logical element (i, jp):
+// jp = ia + Ia_pad * o with ia the index of the fastest mode a and o running
+// mixed-radix over the remaining modes in increasing order; j is the Eq.
+// kolda_mapping column of those indices; zero where i >= I, jp >= Jp or
+// ia >= Ia.  Splits are taken from the FP64 value.
 template <int PREC>
-__global__ void split_unfold_kernel(const double* __restrict__ Tn, int64_t I, int64_t J, int64_t Ia,
-                                    int64_t Ia_pad, int64_t Jp, UnfoldMap mp, const int* __restrict__ rowexp,
-                                    void* p0, void* p1, void* p2, void* p3) {
-  const int64_t total = I * Jp;
+__global__ void tile_unfold_kernel(const double* __restrict__ Tn, int64_t I, int64_t J, int64_t Ia, int64_t Ia_pad,
+                                   int64_t Jp, UnfoldMap mp, const int* __restrict__ rowexp, int BN, int tiles_n,
+                                   int64_t nkt, unsigned char* __restrict__ Tt) {
+  constexpr int EB = (PREC == JKCALS_TF32 || PREC == JKCALS_3XTF32) ? 4 : 2;
+  constexpr int ROW = PREC == JKCALS_EXACT_BF16 ? 64 : 128;
+  constexpr int BK = ROW / EB;
+  constexpr int NS = PREC == JKCALS_EXACT_BF16 ? 4 : (PREC == JKCALS_SPLIT_BF16 ? 3 : (PREC == JKCALS_3XTF32 ? 2 : 1));
+  const int64_t cols = nkt * BK;
+  const int64_t total = (int64_t)tiles_n * BN * cols;
+  const int64_t part_bytes = (int64_t)BN * ROW;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
        e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = e / Jp;
-    const int64_t jp = e - i * Jp;
-    const int64_t o = jp / Ia_pad;
-    const int64_t ia = jp - o * Ia_pad;
+    const int64_t i = e / cols;
+    const int64_t jp = e - i * cols;
     double x = 0.0;
-    if (ia < Ia) {
-      int64_t j = ia * mp.sa, rem = o;
-      for (int t = 0; t < mp.nq; ++t) {
-        const int64_t qq = rem / mp.qd[t];
-        j += (rem - qq * mp.qd[t]) * mp.qs[t];
-        rem = qq;
+    if (i < I && jp < Jp) {
+      const int64_t o = jp / Ia_pad;
+      const int64_t ia = jp - o * Ia_pad;
+      if (ia < Ia) {
+        int64_t j = ia * mp.sa, rem = o;
+        for (int t = 0; t < mp.nq; ++t) {
+          const int64_t qq = rem / mp.qd[t];
+          j += (rem - qq * mp.qd[t]) * mp.qs[t];
+          rem = qq;
+        }
+        x = Tn[i * J + j];
       }
-      x = Tn[i * J + j];
     }
+    float v[NS];
     if constexpr (PREC == JKCALS_TF32 || PREC == JKCALS_3XTF32) {
       const float h = tf32_rna((float)x);
-      static_cast<float*>(p0)[e] = h;
-      if constexpr (PREC == JKCALS_3XTF32) static_cast<float*>(p1)[e] = tf32_rna((float)(x - (double)h));
+      v[0] = h;
+      if constexpr (NS > 1) v[1] = tf32_rna((float)(x - (double)h));
     } else if constexpr (PREC == JKCALS_EXACT_BF16) {
       // x = 2^(F-7) (s0 + s1 2^-7 + s2 2^-14 + s3 2^-21), |s_k| <= 128, stored as s_k 2^(-7k)
-      double y = ldexp(x, kSliceBits - rowexp[i]);
+      double y = i < I ? ldexp(x, kSliceBits - rowexp[i]) : 0.0;
       const double s0 = rint(y);
       y = (y - s0) * 128.0;
       const double s1 = rint(y);
@@ -73,19 +93,31 @@ __global__ void split_unfold_kernel(const double* __restrict__ Tn, int64_t I, in
       const double s2 = rint(y);
       y = (y - s2) * 128.0;
       const double s3 = rint(y);
-      static_cast<__nv_bfloat16*>(p0)[e] = __double2bfloat16(s0);
-      static_cast<__nv_bfloat16*>(p1)[e] = __double2bfloat16(s1 / 128.0);
-      static_cast<__nv_bfloat16*>(p2)[e] = __double2bfloat16(s2 / 16384.0);
-      static_cast<__nv_bfloat16*>(p3)[e] = __double2bfloat16(s3 / 2097152.0);
+      v[0] = (float)s0;
+      v[1] = (float)(s1 / 128.0);
+      v[2] = (float)(s2 / 16384.0);
+      v[3] = (float)(s3 / 2097152.0);
     } else {
-      const __nv_bfloat16 h = __double2bfloat16(x);
-      static_cast<__nv_bfloat16*>(p0)[e] = h;
-      if constexpr (PREC == JKCALS_SPLIT_BF16) {
-        const double r1 = x - (double)__bfloat162float(h);
-        const __nv_bfloat16 m = __double2bfloat16(r1);
-        static_cast<__nv_bfloat16*>(p1)[e] = m;
-        static_cast<__nv_bfloat16*>(p2)[e] = __double2bfloat16(r1 - (double)__bfloat162float(m));
+      const float h = __bfloat162float(__double2bfloat16(x));
+      v[0] = h;
+      if constexpr (NS > 1) {
+        const double r1 = x - (double)h;
+        const float m = __bfloat162float(__double2bfloat16(r1));
+        v[1] = m;
+        v[2] = __bfloat162float(__double2bfloat16(r1 - (double)m));
       }
+    }
+    const int64_t tn = i / BN, ks = jp / BK;
+    const int r = (int)(i - tn * BN), col = (int)(jp - ks * BK);
+    const int64_t tile = (tn * nkt + ks) * NS * part_bytes;
+    const int64_t off = swizzled_offset(r, col * EB, ROW);
+#pragma unroll
+    for (int p = 0; p < NS; ++p) {
+      unsigned char* dst = Tt + tile + p * part_bytes + off;
+      if constexpr (EB == 4)
+        *reinterpret_cast<float*>(dst) = v[p];
+      else
+        *reinterpret_cast<__nv_bfloat16*>(dst) = __float2bfloat16_rn(v[p]);   // exact: v[p] is a BF16 value
     }
   }
 }
@@ -129,30 +161,28 @@ cudaError_t launch_row_exponent(const double* Tn64, int64_t I, int64_t J, int* r
   return cudaGetLastError();
 }
 
-cudaError_t launch_split_unfold(int precision, const double* Tn64, int64_t I, int64_t J, int64_t Ia,
-                                int64_t Ia_pad, int64_t Jp, const UnfoldMap& mp, const int* rowexp,
-                                void* const* parts, cudaStream_t s) {
-  const unsigned g = grid_for(I * Jp);
+cudaError_t launch_tile_unfold(int precision, const double* Tn64, int64_t I, int64_t J, int64_t Ia, int64_t Ia_pad,
+                               int64_t Jp, const UnfoldMap& mp, const int* rowexp, int BN, int tiles_n, int64_t nkt,
+                               void* Tt, cudaStream_t s) {
+  const unsigned g = grid_for((int64_t)tiles_n * BN * nkt * form_bk(precision));
+  unsigned char* out = static_cast<unsigned char*>(Tt);
   switch (precision) {
     case JKCALS_TF32:
-      split_unfold_kernel<JKCALS_TF32><<<g, 256, 0, s>>>(Tn64, I, J, Ia, Ia_pad, Jp, mp, rowexp, parts[0], nullptr,
-                                                         nullptr, nullptr);
+      tile_unfold_kernel<JKCALS_TF32><<<g, 256, 0, s>>>(Tn64, I, J, Ia, Ia_pad, Jp, mp, rowexp, BN, tiles_n, nkt, out);
       break;
     case JKCALS_3XTF32:
-      split_unfold_kernel<JKCALS_3XTF32><<<g, 256, 0, s>>>(Tn64, I, J, Ia, Ia_pad, Jp, mp, rowexp, parts[0],
-                                                           parts[1], nullptr, nullptr);
+      tile_unfold_kernel<JKCALS_3XTF32><<<g, 256, 0, s>>>(Tn64, I, J, Ia, Ia_pad, Jp, mp, rowexp, BN, tiles_n, nkt, out);
       break;
     case JKCALS_BF16:
-      split_unfold_kernel<JKCALS_BF16><<<g, 256, 0, s>>>(Tn64, I, J, Ia, Ia_pad, Jp, mp, rowexp, parts[0], nullptr,
-                                                         nullptr, nullptr);
+      tile_unfold_kernel<JKCALS_BF16><<<g, 256, 0, s>>>(Tn64, I, J, Ia, Ia_pad, Jp, mp, rowexp, BN, tiles_n, nkt, out);
       break;
     case JKCALS_SPLIT_BF16:
-      split_unfold_kernel<JKCALS_SPLIT_BF16><<<g, 256, 0, s>>>(Tn64, I, J, Ia, Ia_pad, Jp, mp, rowexp, parts[0],
-                                                               parts[1], parts[2], nullptr);
+      tile_unfold_kernel<JKCALS_SPLIT_BF16><<<g, 256, 0, s>>>(Tn64, I, J, Ia, Ia_pad, Jp, mp, rowexp, BN, tiles_n, nkt,
+                                                              out);
       break;
     case JKCALS_EXACT_BF16:
-      split_unfold_kernel<JKCALS_EXACT_BF16><<<g, 256, 0, s>>>(Tn64, I, J, Ia, Ia_pad, Jp, mp, rowexp, parts[0],
-                                                               parts[1], parts[2], parts[3]);
+      tile_unfold_kernel<JKCALS_EXACT_BF16><<<g, 256, 0, s>>>(Tn64, I, J, Ia, Ia_pad, Jp, mp, rowexp, BN, tiles_n, nkt,
+                                                              out);
       break;
     default:
       return cudaErrorInvalidValue;
