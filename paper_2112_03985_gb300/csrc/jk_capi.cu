@@ -169,7 +169,6 @@ jkcals_status make_tc_plan(jkcals_ctx* h) {
   const int nsplit = tc::form_nsplit(prec), bk = tc::form_bk(prec), chunk = tc::form_chunk(prec);
   const int row = tc::form_row_bytes(prec);
   const int bn_max = (nsplit >= 3) ? 160 : 256;
-  const int n_acc = exact ? 3 : 1;
   for (int n = 0; n < h->N; ++n) {
     tc::TcPlan& p = h->tcplan[n];
     const int64_t I = h->dims[n];
@@ -184,36 +183,35 @@ jkcals_status make_tc_plan(jkcals_ctx* h) {
     p.Jp = (int64_t)p.Ia_pad * (h->J[n] / h->dims[p.a_mode]);
     if (p.Jp > 2147483647LL - 4096)   // the kernel indexes columns in 32 bits
       return fail(JKCALS_ERR_UNSUPPORTED, "tensor-core forms need prod of the other dims < 2^31");
-    const int64_t nt = (I + bn_max - 1) / bn_max;
-    p.BN = (int)round_up((I + nt - 1) / nt, 16);
+    // N tile: one tile of a multiple of 32 rows when I_n <= 128 for the split
+    // forms (their part products then stack along N into few, wide MMAs),
+    // otherwise balanced tiles of at most bn_max rows
+    if (nsplit > 1 && I <= 128) {
+      p.BN = (int)round_up(I, 32);
+    } else {
+      const int64_t nt = (I + bn_max - 1) / bn_max;
+      p.BN = (int)round_up((I + nt - 1) / nt, 16);
+    }
     p.tiles_c = (h->C + 127) / 128;
     p.tiles_n = (int)((I + p.BN - 1) / p.BN);
-    // Shared memory: a double-buffered A ring (the producers stay one tile
-    // ahead), a TMA-fed B ring as deep as fits (up to 6) to hide the latency of
-    // T tiles, and, when that still leaves at least 3 B stages, the mode-a
-    // factor rows of the CTA's 128 columns (FP32 hi, BF16 lo), staged once.
+    if (tc::build_mma_list(prec, p) != JKCALS_OK) return fail(JKCALS_ERR_UNSUPPORTED, "accumulators exceed TMEM");
+    // Shared memory: the mode-a factor rows of the CTA's 128 columns (FP32 hi,
+    // BF16 lo) staged once when they fit beside two pipeline stages; then as
+    // many stages as fit, up to 4.
     p.ua_parts = exact ? 2 : 1;
     p.ua_stride = p.Ia_pad + 4;   // 16-byte skew between FP32 rows: fewer bank conflicts
-    p.stages_a = 2;
-    auto fit_b = [&](int ua) {
-      p.ua_smem = ua;
-      p.stages_b = 1;
-      while (p.stages_b < 6) {
-        ++p.stages_b;
-        if (tc::tc_smem_bytes(p) > kSmemOptin) {
-          --p.stages_b;
-          break;
-        }
-      }
-      return p.stages_b;
-    };
-    if (fit_b(1) < 3) fit_b(0);
-    if (p.stages_b < 2 || tc::tc_smem_bytes(p) > kSmemOptin)
+    p.stages = 2;
+    p.ua_smem = 1;
+    if (tc::tc_smem_bytes(p) > kSmemOptin) p.ua_smem = 0;
+    if (tc::tc_smem_bytes(p) > kSmemOptin)
       return fail(JKCALS_ERR_UNSUPPORTED, "tensor-core tile does not fit shared memory");
-    p.acc_cols = (int)round_up(p.BN, 32);
-    p.tmem_cols = 32;
-    while (p.tmem_cols < n_acc * p.acc_cols) p.tmem_cols *= 2;
-    if (p.tmem_cols > 512) return fail(JKCALS_ERR_UNSUPPORTED, "accumulators exceed TMEM");
+    while (p.stages < 4) {
+      ++p.stages;
+      if (tc::tc_smem_bytes(p) > kSmemOptin) {
+        --p.stages;
+        break;
+      }
+    }
     const int64_t base = (int64_t)p.tiles_c * p.tiles_n;
     const int64_t ksteps = (p.Jp + bk - 1) / bk;
     int64_t S = h->opt.splits > 0 ? h->opt.splits : std::max<int64_t>(1, h->num_sms / base);
@@ -298,11 +296,13 @@ jkcals_status enqueue_mttkrp(jkcals_ctx* h, int n, double* const* U, float* cons
   a.C = h->C;
   a.BN = p.BN;
   a.tmem_cols = p.tmem_cols;
-  a.acc_cols = p.acc_cols;
+  a.nlev = p.nlev;
+  a.lstride = p.lstride;
+  a.merged = p.merged;
+  a.mma = p.mma;
   a.nkt = p.nkt;
   a.Tt = static_cast<const unsigned char*>(h->Tt[n]);
-  a.stages_a = p.stages_a;
-  a.stages_b = p.stages_b;
+  a.stages = p.stages;
   a.Ia_pad = p.Ia_pad;
   a.UTa = UT[p.a_mode];
   a.UTa_lo = UTlo[p.a_mode];

@@ -57,16 +57,27 @@ struct ModePlan {
 };
 
 namespace tc {
+// MMAs of one 32-byte K slice of a stage: entry m multiplies A part a[m] by
+// n[m] consecutive B parts starting at b[m] (descriptor offsets in 16-byte
+// units from the stage bases) into TMEM columns d[m] onward; bit m of first:
+// the MMA overwrites those columns on the first K slice of the chain.
+struct MmaList {
+  int n;
+  uint32_t a[10], b[10], d[10], idesc[10];
+  uint32_t first;
+};
+
 // Tensor-core form of one mode (see jk_tc.cuh).
 struct TcPlan {
   int BN;          // N tile (rows of T_(n)), multiple of 16, <= 256
   int tiles_c;     // ceil(C / 128)
   int tiles_n;     // ceil(I_n / BN)
   int splits;      // split-K factor
-  int stages_a;    // A ring depth (producer-built Khatri-Rao tiles)
-  int stages_b;    // B ring depth (TMA-loaded tiles of T_(n))
-  int tmem_cols;   // power of two >= accumulators * acc_cols
-  int acc_cols;    // TMEM column stride between accumulators
+  int stages;      // pipeline depth (stages of A and B tiles)
+  int tmem_cols;   // power of two >= nlev * lstride
+  int nlev;        // accumulators (product levels) in TMEM
+  int lstride;     // TMEM columns between accumulators (multiple of 32)
+  int merged;      // exact form with BN > 128: levels 2 and 3 share an accumulator
   int nsplit;      // operand parts of the form
   int row_bytes;   // bytes of K per operand row and stage (128 or 64)
   int a_mode;      // fastest other mode
@@ -77,6 +88,7 @@ struct TcPlan {
   int ua_smem;     // 1: the CTA keeps its 128 factor rows of mode a (hi, lo) in shared memory
   int ua_stride;   // floats per staged FP32 row (Ia_pad plus a bank skew)
   int ua_parts;    // staged copies: 1 (FP32 hi) or 2 (plus BF16 lo)
+  MmaList mma;     // MMAs per K slice
 };
 }  // namespace tc
 

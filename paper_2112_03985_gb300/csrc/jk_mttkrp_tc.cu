@@ -8,40 +8,52 @@
 // submodels and its N dimension over the I_n rows of the mode (<= 256 per
 // tile), while the long contraction over J is split across CTAs (split-K).
 //
-// Roles inside one CTA (10 warps, one CTA per SM):
-//   warp 0     TMA producer: streams BN-row tiles of the (pre-split) unfolding
-//              T_(n) into a ring of B stages.  The unfolding is stored pre-tiled
-//              in the exact shared-memory image of a stage (K-major, 128- or
-//              64-byte swizzle), so each stage is one contiguous bulk copy per
-//              part instead of BN short rows strided across T_(n).
-//   warp 1     owns TMEM; one lane issues tcgen05.mma (kind::tf32, or
-//              kind::f16 with BF16 operands) for every (A-part, B-part) pair
-//              of the precision form, accumulating in FP32 in TMEM.
-//   warps 2-9  build the 128 x BK tile of KRP_n^T into a ring of A stages,
-//              straight in the UMMA K-major swizzled layout: element (c, j) =
-//              U_a^T(c, i_a(j)) * prod_{other k} U_k^T(c, i_k(j)), in FP32 from
-//              transposed FP32 copies of the factor multi-matrices (the rows of
-//              the fastest mode a are staged in shared memory once per CTA),
-//              then split into the form's parts.  After the main loop they drain
-//              TMEM (tcgen05.ld 32x32b) and write this split's partial of Mbar_n.
-// The A and B rings are separate: the small TMA-fed B ring gets as many stages
-// as fit, so T-tile latency is hidden even when the A ring is double-buffered.
+// Roles inside one CTA (12 warps, one CTA per SM):
+//   warp 0      TMA producer: streams BN-row tiles of the (pre-split) unfolding
+//               T_(n) into the B half of each pipeline stage.  The unfolding is
+//               stored pre-tiled in the exact shared-memory image of a stage
+//               (K-major, 128- or 64-byte swizzle), so each stage is one
+//               contiguous bulk copy per part instead of BN short rows strided
+//               across T_(n).
+//   warp 1      owns TMEM; one lane issues the stage's tcgen05.mma list
+//               (kind::tf32, or kind::f16 with BF16 operands), FP32 accumulators
+//               in TMEM.  It is alone on its scheduler (warps 5 and 9, which share
+//               it, only sleep until the epilogue): busy warps there would cut its
+//               issue rate several-fold and starve the tensor pipe.
+//   warps 2, 3, 4, 6, 7, 8, 10, 11
+//               build the 128 x BK tile of KRP_n^T into the A half of each stage,
+//               straight in the UMMA K-major swizzled layout: element (c, j) =
+//               U_a^T(c, i_a(j)) * prod_{other k} U_k^T(c, i_k(j)), in FP32 from
+//               transposed FP32 copies of the factor multi-matrices (the rows of
+//               the fastest mode a are staged in shared memory once per CTA; the
+//               remaining modes' entries are fetched one k-step ahead), then
+//               split into the form's parts.
+//   warps 4-11  after the main loop drain TMEM (tcgen05.ld 32x32b, two warps per
+//               lane quarter) and write this split's partial of Mbar_n.
 // The Khatri-Rao product never exists in global memory.
+//
+// Split forms: with operand parts A_s, B_t (s, t < P), the products A_s B_t with
+// s + t < P are accumulated per level l = s + t in TMEM columns [l L, l L + BN)
+// (L = lstride).  The B parts of a stage are contiguous BN-row blocks, so one
+// MMA of A_s against the parts t0..t1 (N = (t1 - t0 + 1) BN <= 256) lands part
+// t in level s + t directly when L = BN: the exact form needs 4 MMAs per K slice
+// instead of 10 for BN = 64.
 //
 // Exact-chain form (JKCALS_EXACT_BF16): every operand value x of a row whose
 // magnitudes stay below 2^E is written as x = 2^(E-7) (s0 + s1/2^7 + s2/2^14 +
-// s3/2^21) with integers |s_k| <= 128 (round-to-nearest extraction, exact in
-// FP32) and stored as BF16 s_k * 2^(-7k).  Products of level 0 (s0 t0) and of
-// level 1 (s0 t1 + s1 t0) are integer multiples of 1 and 2^-7 whose chain sums
-// stay below 2^24 units for chains of <= 1024 columns, so they accumulate
-// exactly in FP32 TMEM; levels 2-3 share a third accumulator whose truncation
-// is scaled by 2^-14.  The Khatri-Rao entries themselves are formed as
-// unevaluated FP32 pairs (error-free FMA products of hi/lo factor copies).  The
-// epilogue adds the three accumulators with TwoSum into an FP32 pair and
+// s3/2^21) with integers |s_0| <= 128, |s_k| <= 64 (round-to-nearest
+// extraction, exact in FP32) and stored as BF16 s_k * 2^(-7k).  Products of
+// level 0 (s0 t0) and of level 1 (s0 t1 + s1 t0) are integer multiples of 1 and
+// 2^-7 whose chain sums stay below 2^24 units for chains of <= 1024 columns, so
+// they accumulate exactly in FP32 TMEM; levels 2 and 3 carry truncation scaled
+// by 2^-14.  The Khatri-Rao entries themselves are formed as unevaluated FP32
+// pairs (error-free FMA products of hi/lo factor copies), with packed f32x2
+// arithmetic.  The epilogue adds the levels with TwoSum into an FP32 pair and
 // applies 2^(E_c - 7) 2^(F_i - 7).
 //
-// Synchronisation: mbarriers per A stage (tile written / consumed), per B stage
-// (tile landed / consumed) and one for the accumulator.  Every wait is bounded
+// Synchronisation: per stage one "full" mbarrier (the producer warps' arrivals
+// plus the TMA arrival and its bytes) and one "empty" mbarrier (the MMAs'
+// commit), so the MMA lane waits once per stage; one more for the accumulator.  Every wait is bounded
 // by a wall-clock limit; on expiry the CTA records an error code, stops, waits
 // (bounded) for its own TMA copies and MMAs, frees its TMEM and returns.
 #include <cuda_bf16.h>
@@ -56,11 +68,20 @@ namespace {
 
 using namespace ptx;
 
-constexpr int kProducerWarps = 8;                    // two per scheduler: hides load latency
-constexpr int kThreads = 32 * (2 + kProducerWarps);  // + the TMA warp and the MMA warp
-constexpr int kProducerWarp0 = 2;
+// Warp roles.  A warp runs on scheduler (warp id mod 4); the MMA warp must not
+// share its scheduler with busy warps (four arithmetic warps there cut its
+// issue rate about fourfold), so warps 5 and 9 only drain TMEM.
+//   0: TMA  1: MMA  2, 3, 4, 6, 7, 8, 10, 11: Khatri-Rao producers
+//   4..11: epilogue (two warps per TMEM lane quarter)
+constexpr int kWarps = 12;
+constexpr int kThreads = 32 * kWarps;
+constexpr int kProducerWarps = 8;
 constexpr int kRowsPerWarp = 128 / kProducerWarps;   // rows of the A tile per producer warp
+constexpr int kEpilogueWarp0 = 4;
+__device__ __forceinline__ bool is_producer_warp(int w) { return w >= 2 && (w & 3) != 1; }
+__device__ __forceinline__ int producer_index(int w) { return w - 2 - (w > 5) - (w > 9); }
 constexpr int kRowsM = 128;                          // MMA M
+constexpr int kMaxMma = 10;                          // entries of an MmaList
 
 // UMMA shared-memory descriptor: K-major operand, ROW-byte swizzle (128 -> 2,
 // 64 -> 4), 8-row groups 8*ROW bytes apart (SBO), version 1 (tcgen05).
@@ -69,12 +90,6 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
   constexpr uint64_t layout = ROW == 128 ? 2 : 4;
   return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)((8 * ROW) >> 4) << 32) |
          ((uint64_t)1 << 46) | (layout << 61);
-}
-
-// Instruction descriptor: FP32 accumulator, A/B format fmt (TF32 = 2 under
-// kind::tf32, BF16 = 1 under kind::f16), both K-major, N and M.
-__device__ __forceinline__ uint32_t make_idesc(uint32_t fmt, uint32_t M, uint32_t N) {
-  return (1u << 4) | (fmt << 7) | (fmt << 10) | ((N >> 3) << 17) | ((M >> 4) << 24);
 }
 
 __device__ __forceinline__ float tf32_rna(float x) {
@@ -86,12 +101,27 @@ __device__ __forceinline__ float tf32_rna(float x) {
 // 2^k as FP32 for k in [-126, 127]
 __device__ __forceinline__ float pow2f(int k) { return __int_as_float((127 + k) << 23); }
 
-// Smallest E (clamped to [-110, 110]) with |values| < 2^E given a bound b >= 0.
-__device__ __forceinline__ int bound_exponent(double b) {
-  if (!(b > 0.0)) return 0;
-  int e;
-  frexp(b, &e);   // b = m 2^e, m in [0.5, 1)
-  return e < -110 ? -110 : (e > 110 ? 110 : e);
+// Smallest E (clamped to [-110, 110]) with prod_k x_k < 2^E for the maxima
+// x_k >= 0 of the factors of one Khatri-Rao column (0 when a factor is zero).
+// Exponents add exactly; the mantissas (in [0.5, 1)) multiply in FP32, whose
+// rounding is monotonic, so the bound can only come out one binade looser,
+// never tighter.  No FP64: its pipe is narrow on this part.
+__device__ __forceinline__ int bound_exponent_prod(float x0, const float* const* more, int nmore, int c) {
+  if (!(x0 > 0.f)) return 0;
+  int e, esum;
+  float m = frexpf(x0, &esum);
+#pragma unroll
+  for (int t = 0; t < kMaxModes - 2; ++t) {
+    if (t < nmore) {
+      const float x = __ldg(more[t] + c);
+      if (!(x > 0.f)) return 0;
+      m *= frexpf(x, &e);
+      esum += e;
+    }
+  }
+  frexpf(m, &e);
+  esum += e;
+  return esum < -110 ? -110 : (esum > 110 ? 110 : esum);
 }
 
 // BF16 bit patterns of values that BF16 represents exactly (the slices and
@@ -100,29 +130,44 @@ __device__ __forceinline__ uint32_t pack_bf16_exact(float lo, float hi) {
   return __byte_perm(__float_as_uint(lo), __float_as_uint(hi), 0x7632);
 }
 
-// Split one FP32 value (plus a low part for the exact-chain form) into the
-// form's parts, returned as FP32 values that the part's storage represents exactly.
+// ---- packed FP32 pairs (two lanes of f32x2 arithmetic, round to nearest) ----
+struct f2 {
+  uint64_t r;
+};
+__device__ __forceinline__ f2 f2_pack(float lo, float hi) {
+  f2 v;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(v.r) : "f"(lo), "f"(hi));
+  return v;
+}
+__device__ __forceinline__ void f2_unpack(f2 v, float& lo, float& hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v.r));
+}
+__device__ __forceinline__ f2 f2_add(f2 a, f2 b) {
+  f2 d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d.r) : "l"(a.r), "l"(b.r));
+  return d;
+}
+__device__ __forceinline__ f2 f2_sub(f2 a, f2 b) {
+  f2 d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d.r) : "l"(a.r), "l"(b.r));
+  return d;
+}
+__device__ __forceinline__ f2 f2_mul(f2 a, f2 b) {
+  f2 d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d.r) : "l"(a.r), "l"(b.r));
+  return d;
+}
+__device__ __forceinline__ f2 f2_fma(f2 a, f2 b, f2 c) {
+  f2 d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d.r) : "l"(a.r), "l"(b.r), "l"(c.r));
+  return d;
+}
+
+// Split one FP32 value into the parts of a non-exact form, returned as FP32
+// values that the part's storage represents exactly.
 template <class Cfg>
-__device__ __forceinline__ void split_value(float v, float vl, float scale, float (&p)[4]) {
-  if constexpr (Cfg::exact) {
-    // y = (v + vl) * scale lies in [-128, 128].  (r + M_k) - M_k with M_k =
-    // 1.5 * 2^(23 - 7k) rounds r to the nearest multiple of 2^(-7k) (FP32
-    // round-to-nearest), so each slice comes out already scaled by 2^(-7k);
-    // every step is exact except adding the low part after the first slice
-    // (error below 2^-25 of the grid unit).
-    float y = __fmul_rn(v, scale);
-    const float s0 = __fsub_rn(__fadd_rn(y, 12582912.f), 12582912.f);          // M = 1.5 * 2^23
-    y = __fadd_rn(__fsub_rn(y, s0), __fmul_rn(vl, scale));
-    const float s1 = __fsub_rn(__fadd_rn(y, 98304.f), 98304.f);                 // M = 1.5 * 2^16
-    y = __fsub_rn(y, s1);
-    const float s2 = __fsub_rn(__fadd_rn(y, 768.f), 768.f);                     // M = 1.5 * 2^9
-    y = __fsub_rn(y, s2);
-    const float s3 = __fsub_rn(__fadd_rn(y, 6.f), 6.f);                         // M = 1.5 * 2^2
-    p[0] = s0;
-    p[1] = s1;
-    p[2] = s2;
-    p[3] = s3;
-  } else if constexpr (Cfg::kind == kKindTF32) {
+__device__ __forceinline__ void split_value(float v, float (&p)[4]) {
+  if constexpr (Cfg::kind == kKindTF32) {
     const float h = tf32_rna(v);
     p[0] = h;
     if constexpr (Cfg::nsplit > 1) p[1] = tf32_rna(v - h);
@@ -138,9 +183,51 @@ __device__ __forceinline__ void split_value(float v, float vl, float scale, floa
   }
 }
 
+// Exact-chain form, two Khatri-Rao entries at once: the pairs (u_e + ul_e) *
+// (qh + ql) as unevaluated FP32 pairs (error-free FMA products), scaled by the
+// row's power of two into [-128, 128] and cut into four slices on the grids
+// 2^(-7k): (r + M_k) - M_k with M_k = 1.5 * 2^(23 - 7k) rounds r to the nearest
+// multiple of 2^(-7k).  Every step is exact except adding the low part after
+// the first slice (error below 2^-25 of the grid unit).  Returns the BF16
+// patterns of the two entries' slices, one 32-bit word per slice.
+__device__ __forceinline__ void exact_slices2(f2 u, f2 ul, f2 qh2, f2 nqh2, f2 ql2, f2 sc2, uint32_t (&w)[4]) {
+  const f2 p = f2_mul(u, qh2);
+  const f2 e1n = f2_fma(u, nqh2, p);                           // p - u qh, exact
+  const f2 e2 = f2_fma(u, ql2, f2_mul(ul, qh2));               // u ql + ul qh
+  const f2 vl = f2_sub(e2, e1n);
+  const f2 m0 = f2_pack(12582912.f, 12582912.f);               // 1.5 * 2^23
+  const f2 m1 = f2_pack(98304.f, 98304.f);                     // 1.5 * 2^16
+  const f2 m2 = f2_pack(768.f, 768.f);                         // 1.5 * 2^9
+  const f2 m3 = f2_pack(6.f, 6.f);                             // 1.5 * 2^2
+  f2 y = f2_mul(p, sc2);
+  const f2 s0 = f2_sub(f2_add(y, m0), m0);
+  y = f2_fma(vl, sc2, f2_sub(y, s0));
+  const f2 s1 = f2_sub(f2_add(y, m1), m1);
+  y = f2_sub(y, s1);
+  const f2 s2 = f2_sub(f2_add(y, m2), m2);
+  y = f2_sub(y, s2);
+  const f2 s3 = f2_sub(f2_add(y, m3), m3);
+  float a, b;
+  f2_unpack(s0, a, b);
+  w[0] = pack_bf16_exact(a, b);
+  f2_unpack(s1, a, b);
+  w[1] = pack_bf16_exact(a, b);
+  f2_unpack(s2, a, b);
+  w[2] = pack_bf16_exact(a, b);
+  f2_unpack(s3, a, b);
+  w[3] = pack_bf16_exact(a, b);
+}
+
+// Error-free product of the pairs (qh + ql)(bh + bl), renormalised.
+__device__ __forceinline__ void pair_mul(float& qh, float& ql, float bh, float bl) {
+  const float pq = __fmul_rn(qh, bh);
+  const float eq = __fadd_rn(__fmaf_rn(qh, bh, -pq), __fmaf_rn(qh, bl, __fmul_rn(ql, bh)));
+  qh = pq;
+  ql = eq;
+}
+
 template <class Cfg>
-__global__ void __launch_bounds__(kThreads, 1)
-    mttkrp_tc_kernel(const TcArgs a) {
+__global__ void __launch_bounds__(kThreads, 1) mttkrp_tc_kernel(const TcArgs a) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem =
       reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -150,27 +237,26 @@ __global__ void __launch_bounds__(kThreads, 1)
   constexpr int CHUNK = 16 / Cfg::elem;          // elements per 16-byte chunk
   constexpr int CPR = ROW / 16;                  // chunks per row
   constexpr int RPI = 32 / CPR;                  // rows covered by one warp instruction
-  constexpr int ROWS_PER_THREAD = kRowsPerWarp / RPI;  // rows per producer thread per stage
+  constexpr int RPT = kRowsPerWarp / RPI;        // rows per producer thread per stage
+  static_assert(RPT >= 1 && RPT * RPI == kRowsPerWarp, "producer mapping");
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t a_bytes = kRowsM * ROW;
   const uint32_t b_bytes = (uint32_t)a.BN * ROW;
   const uint32_t a_stage = NS * a_bytes, b_stage = NS * b_bytes;
-  const int SA = a.stages_a, SB = a.stages_b;
-  // layout: A ring | B ring | staged mode-a rows (FP32 hi, BF16 lo) | barriers
-  unsigned char* a_ring = smem;
-  unsigned char* b_ring = smem + (size_t)SA * a_stage;
-  float* ua_hi = reinterpret_cast<float*>(b_ring + (size_t)SB * b_stage);
+  const uint32_t stage_bytes = a_stage + b_stage;   // a multiple of 1024
+  const int S = a.stages;
+  // layout: S stages of (A parts | B parts) | staged mode-a rows (FP32 hi, BF16 lo) | barriers
+  unsigned char* ring = smem;
+  float* ua_hi = reinterpret_cast<float*>(ring + (size_t)S * stage_bytes);
   // staged rows: FP32 with a 16-byte skew (ua_stride floats), BF16 low parts
   // densely (Ia_pad elements: a multiple of 8, so rows stay 16-byte aligned)
   const size_t ua_n = a.ua_smem ? (size_t)kRowsM * a.ua_stride : 0;
   const size_t ua_ln = (a.ua_smem && Cfg::exact) ? (size_t)kRowsM * a.Ia_pad : 0;
   __nv_bfloat16* ua_lo = reinterpret_cast<__nv_bfloat16*>(ua_hi + ua_n);
   uint64_t* bars = reinterpret_cast<uint64_t*>(ua_lo + ua_ln);
-  uint64_t* full_a = bars;
-  uint64_t* empty_a = bars + SA;
-  uint64_t* full_b = bars + 2 * SA;
-  uint64_t* empty_b = bars + 2 * SA + SB;
-  uint64_t* accum = bars + 2 * SA + 2 * SB;
+  uint64_t* full = bars;          // stage written: producer warps + the TMA arrival and its bytes
+  uint64_t* empty = bars + S;     // stage consumed: the MMAs' commit
+  uint64_t* accum = bars + 2 * S;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accum + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
@@ -182,13 +268,9 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int nk = (je > jb) ? (int)((je - jb + BK - 1) / BK) : 0;
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < SA; ++s) {
-      mbar_init(&full_a[s], kProducerWarps);   // one arrival per producer warp
-      mbar_init(&empty_a[s], 1);
-    }
-    for (int s = 0; s < SB; ++s) {
-      mbar_init(&full_b[s], 1);
-      mbar_init(&empty_b[s], 1);
+    for (int s = 0; s < S; ++s) {
+      mbar_init(&full[s], kProducerWarps + 1);   // one arrival per producer warp + the TMA thread
+      mbar_init(&empty[s], 1);
     }
     mbar_init(accum, 1);
     *abort_flag = 0;
@@ -207,54 +289,53 @@ __global__ void __launch_bounds__(kThreads, 1)
       // this CTA's first stage image: N tile blockIdx.y, k-step jb / BK
       const unsigned char* src = a.Tt + ((int64_t)blockIdx.y * a.nkt + jb / BK) * (int64_t)b_stage;
       for (int it = 0; it < nk; ++it) {
-        const int s = it % SB;
-        const uint32_t ph = (uint32_t)(it / SB) & 1u;
-        if (!wait_bounded(&empty_b[s], ph ^ 1u, abort_flag, a.err, 1)) break;
-        mbar_arrive_expect_tx(&full_b[s], b_stage);
-        unsigned char* dst = b_ring + (size_t)s * b_stage;
+        const int s = it % S;
+        const uint32_t ph = (uint32_t)(it / S) & 1u;
+        if (!wait_bounded(&empty[s], ph ^ 1u, abort_flag, a.err, 1)) break;
+        mbar_arrive_expect_tx(&full[s], b_stage);
+        unsigned char* dst = ring + (size_t)s * stage_bytes + a_stage;
 #pragma unroll
-        for (int p = 0; p < NS; ++p) bulk_load(dst + p * b_bytes, src + p * b_bytes, b_bytes, &full_b[s]);
+        for (int p = 0; p < NS; ++p) bulk_load(dst + p * b_bytes, src + p * b_bytes, b_bytes, &full[s]);
         src += b_stage;
         issued = it + 1;
       }
-      if (*abort_flag) {
-        // let every copy this thread started land before the CTA exits
-        for (int it = (issued > SB ? issued - SB : 0); it < issued; ++it)
-          wait_drain(&full_b[it % SB], (uint32_t)(it / SB) & 1u);
+      if (*abort_flag && issued > 0) {
+        // let the copies this thread started land before the CTA exits (a
+        // stage's phase may never complete once producers stopped, so wait a
+        // fixed, ample time instead of on the barrier)
+        const uint64_t t0 = global_ns();
+        while (global_ns() - t0 < 200000ull) {
+        }
       }
     }
   } else if (warp == 1) {
     // ---------------- MMA issuer --------------------------------------------------
     if (lane == 0) {
-      const uint32_t idesc = make_idesc(Cfg::fmt, kRowsM, (uint32_t)a.BN);
       // The descriptor's start-address field is (address >> 4) in its low 14
       // bits, so every operand descriptor is the region's base descriptor plus
-      // (byte offset >> 4): one add per MMA instead of rebuilding it.
-      const uint64_t adesc0 = smem_desc<ROW>(smem_u32(a_ring));
-      const uint64_t bdesc0 = smem_desc<ROW>(smem_u32(b_ring));
-      const uint32_t tmem_acc1 = tmem + (uint32_t)a.acc_cols, tmem_acc2 = tmem + 2u * (uint32_t)a.acc_cols;
+      // (byte offset >> 4): the list holds those offsets per MMA.
+      const uint64_t desc0 = smem_desc<ROW>(smem_u32(ring));
+      const int nm = a.mma.n;
       bool ok = true;
       for (int it = 0; it < nk && ok; ++it) {
-        const int sa = it % SA, sb = it % SB;
-        ok = wait_bounded(&full_b[sb], (uint32_t)(it / SB) & 1u, abort_flag, a.err, 2) &&
-             wait_bounded(&full_a[sa], (uint32_t)(it / SA) & 1u, abort_flag, a.err, 3);
+        const int s = it % S;
+        ok = wait_bounded(&full[s], (uint32_t)(it / S) & 1u, abort_flag, a.err, 2);
         if (!ok) break;
         tc_fence_after();
-        const uint64_t ad0 = adesc0 + (uint64_t)(((uint32_t)sa * a_stage) >> 4);
-        const uint64_t bd0 = bdesc0 + (uint64_t)(((uint32_t)sb * b_stage) >> 4);
+        const uint64_t ad0 = desc0 + (uint64_t)(((uint32_t)s * stage_bytes) >> 4);
+        const uint64_t bd0 = ad0 + (uint64_t)(a_stage >> 4);
 #pragma unroll
         for (int kk = 0; kk < ROW / 32; ++kk) {
 #pragma unroll
-          for (int q = 0; q < Cfg::npass; ++q) {
-            const uint64_t ad = ad0 + (uint64_t)((Cfg::pass_a(q) * a_bytes + kk * 32) >> 4);
-            const uint64_t bd = bd0 + (uint64_t)((Cfg::pass_b(q) * b_bytes + kk * 32) >> 4);
-            const uint32_t d = Cfg::pass_acc(q) == 0 ? tmem : (Cfg::pass_acc(q) == 1 ? tmem_acc1 : tmem_acc2);
-            const bool first = (it == 0 && kk == 0 && Cfg::first_of_acc(q));
-            tc_mma<Cfg::kind>(d, ad, bd, idesc, first ? 0u : 1u);
+          for (int m = 0; m < kMaxMma; ++m) {   // static indices: the list stays in the parameter bank
+            if (m < nm) {
+              const bool first = it == 0 && kk == 0 && ((a.mma.first >> m) & 1u);
+              tc_mma<Cfg::kind>(tmem + a.mma.d[m], ad0 + (uint64_t)(a.mma.a[m] + 2 * kk),
+                                bd0 + (uint64_t)(a.mma.b[m] + 2 * kk), a.mma.idesc[m], first ? 0u : 1u);
+            }
           }
         }
-        tc_commit(&empty_a[sa]);
-        tc_commit(&empty_b[sb]);
+        tc_commit(&empty[s]);
       }
       // Always signal the accumulator: its phase completes once every MMA issued
       // above has finished, so on an abort this lane drains them before TMEM is freed.
@@ -262,27 +343,31 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (!ok) wait_drain(accum, 0);
     }
   } else {
-    // ---------------- Khatri-Rao producers (warps 2..9) ------------------------------
-    const int pw = warp - kProducerWarp0;   // 0..kProducerWarps-1
+    bool ok = true;
+    if (is_producer_warp(warp)) {
+    // ---------------- Khatri-Rao producers ------------------------------------------
+    const int pw = producer_index(warp);    // 0..kProducerWarps-1
     const int rg = lane / CPR;              // row within a group of RPI rows
     const int q = lane % CPR;               // 16-byte chunk within the row
     // per-row constants, hoisted out of the k loop
-    bool cval[ROWS_PER_THREAD];
-    float rscale[ROWS_PER_THREAD];
-    uint32_t soff[ROWS_PER_THREAD];                      // swizzled offset in an A tile
-    const float* ra[ROWS_PER_THREAD];                    // global rows of UTa (unstaged path)
-    const float* ral[ROWS_PER_THREAD];
-    const float* rq0[ROWS_PER_THREAD];
-    const float* rq0l[ROWS_PER_THREAD];
-    const float* rq1[ROWS_PER_THREAD];
-    const float* rq1l[ROWS_PER_THREAD];
-    uint32_t ua_row[ROWS_PER_THREAD], ua_rowl[ROWS_PER_THREAD];   // staged rows (shared addresses)
+    bool cval[RPT];
+    float rscale[RPT];
+    uint32_t soff[RPT];                                  // swizzled offset in an A tile
+    const float* ra[RPT];                                // global rows of UTa (unstaged path)
+    const float* ral[RPT];
+    const float* rq0[RPT];
+    const float* rq0l[RPT];
+    const float* rq1[RPT];
+    const float* rq1l[RPT];
+    int crow[RPT];
+    uint32_t ua_row[RPT], ua_rowl[RPT];   // staged rows (shared addresses)
 #pragma unroll
-    for (int rr = 0; rr < ROWS_PER_THREAD; ++rr) {
+    for (int rr = 0; rr < RPT; ++rr) {
       const int m = pw * kRowsPerWarp + rr * RPI + rg;   // row of the A tile = column c0 + m
       const int c = c0 + m;
       cval[rr] = c < a.C;
       const int cc = cval[rr] ? c : 0;
+      crow[rr] = cc;
       const int sw = (ROW == 128) ? (m & 7) : ((m >> 1) & 3);
       soff[rr] = (uint32_t)(m >> 3) * (8u * ROW) + (uint32_t)(m & 7) * ROW + (uint32_t)((q ^ sw) << 4);
       ra[rr] = a.UTa + (int64_t)cc * a.Ia_pad;
@@ -295,23 +380,17 @@ __global__ void __launch_bounds__(kThreads, 1)
       ua_rowl[rr] = smem_u32(ua_lo + (size_t)m * a.Ia_pad);
       rscale[rr] = 1.f;
       if constexpr (Cfg::exact) {
-        if (cval[rr]) {
-          double b = (double)__ldg(a.cmax_a + c);
-#pragma unroll
-          for (int t = 0; t < kMaxModes - 2; ++t)
-            if (t < a.nq) b *= (double)__ldg(a.cmax_q[t] + c);
-          rscale[rr] = pow2f(7 - bound_exponent(b));
-        }
+        if (cval[rr]) rscale[rr] = pow2f(7 - bound_exponent_prod(__ldg(a.cmax_a + c), a.cmax_q, a.nq, c));
       }
     }
     if (a.ua_smem) {
       // stage the CTA's 128 factor rows of mode a once (FP32 hi; BF16 lo for
       // the exact-chain form, which keeps the pair to ~2^-32): the k loop then
       // reads them from shared memory instead of L2
-      const int ptid = threadIdx.x - 32 * kProducerWarp0;
+      const int ptid = pw * 32 + lane;
       const int n4 = a.Ia_pad / 4;
       const int total = kRowsM * n4;
-      constexpr int kU = 4;   // loads in flight per thread
+      constexpr int kU = 2;   // loads in flight per thread
       for (int idx0 = ptid; idx0 < total; idx0 += kU * 32 * kProducerWarps) {
         float4 hv[kU], lv[kU];
 #pragma unroll
@@ -347,8 +426,6 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       asm volatile("bar.sync 1, %0;" ::"r"(32 * kProducerWarps) : "memory");   // producer warps only
     }
-    float qhc[ROWS_PER_THREAD], qlc[ROWS_PER_THREAD];   // cached remaining-mode products
-    bool qstale = true;
     // this thread's column j of the unfolding: j = ia + Ia_pad * o, o mixed-radix
     // over the remaining modes; advanced incrementally by BK per k-step
     const int je32 = (int)je;
@@ -369,13 +446,82 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
       }
     }
-    const uint32_t a_ring_s = smem_u32(a_ring);
-    bool ok = true;
+    // Q(c, o) = prod of the remaining modes' factor entries of row c at the
+    // column's indices, as an FP32 pair; it changes only when the column index
+    // carries out of mode a.  Raw entries of modes t < 2 are loaded one k-step
+    // ahead (pf*), further modes when the product is formed.
+    float qhc[RPT], qlc[RPT];
+    float pf0[RPT], pf0l[RPT], pf1[RPT], pf1l[RPT];
+    auto load_raw = [&](const int (&ix)[kMaxModes - 2]) {
+#pragma unroll
+      for (int rr = 0; rr < RPT; ++rr) {
+        pf0[rr] = pf1[rr] = 1.f;
+        pf0l[rr] = pf1l[rr] = 0.f;
+        if (a.nq > 0) {
+          pf0[rr] = __ldg(rq0[rr] + ix[0]);
+          if constexpr (Cfg::exact) pf0l[rr] = __ldg(rq0l[rr] + ix[0]);
+        }
+        if (a.nq > 1) {
+          pf1[rr] = __ldg(rq1[rr] + ix[1]);
+          if constexpr (Cfg::exact) pf1l[rr] = __ldg(rq1l[rr] + ix[1]);
+        }
+      }
+    };
+    auto form_q = [&](const int (&ix)[kMaxModes - 2]) {
+#pragma unroll
+      for (int rr = 0; rr < RPT; ++rr) {
+        float qh = 1.f, ql = 0.f;
+        if (a.nq > 0) {
+          if constexpr (Cfg::exact) {
+            qh = pf0[rr];
+            ql = pf0l[rr];
+            if (a.nq > 1) pair_mul(qh, ql, pf1[rr], pf1l[rr]);
+          } else {
+            qh = pf0[rr] * pf1[rr];
+          }
+#pragma unroll
+          for (int t = 2; t < kMaxModes - 2; ++t) {
+            if (t < a.nq) {
+              const int64_t idx = (int64_t)crow[rr] * a.qpad[t] + ix[t];
+              const float bh = __ldg(a.UTq[t] + idx);
+              if constexpr (Cfg::exact) {
+                pair_mul(qh, ql, bh, __ldg(a.UTq_lo[t] + idx));
+              } else {
+                qh *= bh;
+              }
+            }
+          }
+        }
+        qhc[rr] = qh;
+        qlc[rr] = ql;
+      }
+    };
+    load_raw(iq);
+    form_q(iq);
+    const uint32_t ring_s = smem_u32(ring);
     for (int it = 0; it < nk && ok; ++it) {
-      const int s = it % SA;
+      const int s = it % S;
+      // next k-step's indices; on a carry fetch its factor entries now
+      int ia_n = ia + BK;
+      int iq_n[kMaxModes - 2];
+#pragma unroll
+      for (int t = 0; t < kMaxModes - 2; ++t) iq_n[t] = iq[t];
+      bool wrap = false;
+      while (ia_n >= a.Ia_pad) {
+        ia_n -= a.Ia_pad;
+        wrap = true;
+#pragma unroll
+        for (int t = 0; t < kMaxModes - 2; ++t) {
+          if (t < a.nq) {
+            if (++iq_n[t] < a.qdims[t]) break;
+            iq_n[t] = 0;
+          }
+        }
+      }
+      if (wrap) load_raw(iq_n);
       // one lane per warp polls the barrier; __syncwarp orders the others after it
       bool got = true;
-      if (lane == 0) got = wait_bounded(&empty_a[s], ((uint32_t)(it / SA) & 1u) ^ 1u, abort_flag, a.err, 4);
+      if (lane == 0) got = wait_bounded(&empty[s], ((uint32_t)(it / S) & 1u) ^ 1u, abort_flag, a.err, 4);
       got = __shfl_sync(0xffffffffu, got, 0);
       __syncwarp();
       if (!got) {
@@ -383,54 +529,56 @@ __global__ void __launch_bounds__(kThreads, 1)
         break;
       }
       const bool jvalid = jcur < je32;
-      if (qstale && jvalid) {
-        // product of the remaining modes' factor entries for each row: it only
-        // changes when the column index carries out of mode a
+      const uint32_t a_tile_s = ring_s + (uint32_t)s * stage_bytes;
 #pragma unroll
-        for (int rr = 0; rr < ROWS_PER_THREAD; ++rr) {
-          float qh = 1.f, ql = 0.f;
-          if (cval[rr]) {
+      for (int rr = 0; rr < RPT; ++rr) {
+        const bool live = jvalid && cval[rr];
+        if constexpr (Cfg::exact) {
+          // CHUNK (8) entries: FP32 hi and BF16 lo of the staged (or global) row
+          float uh[8], ul[8];
+          if (a.ua_smem) {
+            const float4 u0 = lds128(ua_row[rr] + (uint32_t)ia * 4u);
+            const float4 u1 = lds128(ua_row[rr] + (uint32_t)ia * 4u + 16u);
+            const float4 lraw = lds128(ua_rowl[rr] + (uint32_t)ia * 2u);
+            uh[0] = u0.x; uh[1] = u0.y; uh[2] = u0.z; uh[3] = u0.w;
+            uh[4] = u1.x; uh[5] = u1.y; uh[6] = u1.z; uh[7] = u1.w;
+            const uint32_t w4[4] = {__float_as_uint(lraw.x), __float_as_uint(lraw.y), __float_as_uint(lraw.z),
+                                    __float_as_uint(lraw.w)};
 #pragma unroll
-            for (int t = 0; t < kMaxModes - 2; ++t) {
-              if (t < a.nq) {
-                float bh, bl = 0.f;
-                if (t == 0) {
-                  bh = __ldg(rq0[rr] + iq[0]);
-                  if constexpr (Cfg::exact) bl = __ldg(rq0l[rr] + iq[0]);
-                } else if (t == 1) {
-                  bh = __ldg(rq1[rr] + iq[1]);
-                  if constexpr (Cfg::exact) bl = __ldg(rq1l[rr] + iq[1]);
-                } else {
-                  const int64_t idx = (int64_t)(c0 + pw * kRowsPerWarp + rr * RPI + rg) * a.qpad[t] + iq[t];
-                  bh = __ldg(a.UTq[t] + idx);
-                  if constexpr (Cfg::exact) bl = __ldg(a.UTq_lo[t] + idx);
-                }
-                if constexpr (Cfg::exact) {
-                  // error-free product of the pairs (qh + ql)(bh + bl)
-                  const float pq = __fmul_rn(qh, bh);
-                  const float eq = __fadd_rn(__fmaf_rn(qh, bh, -pq), __fmaf_rn(qh, bl, __fmul_rn(ql, bh)));
-                  qh = pq;
-                  ql = eq;
-                } else {
-                  qh *= bh;
-                }
-              }
+            for (int k = 0; k < 4; ++k) {
+              ul[2 * k] = __uint_as_float(w4[k] << 16);
+              ul[2 * k + 1] = __uint_as_float(w4[k] & 0xffff0000u);
             }
+          } else {
+            const float4* src = reinterpret_cast<const float4*>(ra[rr] + ia);
+            const float4* srcl = reinterpret_cast<const float4*>(ral[rr] + ia);
+            const float4 u0 = __ldg(src), u1 = __ldg(src + 1), l0 = __ldg(srcl), l1 = __ldg(srcl + 1);
+            uh[0] = u0.x; uh[1] = u0.y; uh[2] = u0.z; uh[3] = u0.w;
+            uh[4] = u1.x; uh[5] = u1.y; uh[6] = u1.z; uh[7] = u1.w;
+            ul[0] = l0.x; ul[1] = l0.y; ul[2] = l0.z; ul[3] = l0.w;
+            ul[4] = l1.x; ul[5] = l1.y; ul[6] = l1.z; ul[7] = l1.w;
           }
-          qhc[rr] = qh;
-          qlc[rr] = ql;
-        }
-        qstale = false;
-      }
-      const uint32_t a_tile_s = a_ring_s + (uint32_t)s * a_stage;
+          const float qh = live ? qhc[rr] : 0.f, ql = live ? qlc[rr] : 0.f;
+          const f2 qh2 = f2_pack(qh, qh), nqh2 = f2_pack(-qh, -qh), ql2 = f2_pack(ql, ql);
+          const f2 sc2 = f2_pack(rscale[rr], rscale[rr]);
+          uint32_t w[4][4];   // [slice][pair]
 #pragma unroll
-      for (int rr = 0; rr < ROWS_PER_THREAD; ++rr) {
-        float v[CHUNK], vl[CHUNK];
+          for (int e = 0; e < 4; ++e) {
+            uint32_t ws[4];
+            exact_slices2(f2_pack(uh[2 * e], uh[2 * e + 1]), f2_pack(ul[2 * e], ul[2 * e + 1]), qh2, nqh2, ql2, sc2,
+                          ws);
 #pragma unroll
-        for (int e = 0; e < CHUNK; ++e) v[e] = vl[e] = 0.f;
-        if (jvalid && cval[rr]) {
-          const float qh = qhc[rr];
-          if constexpr (!Cfg::exact) {
+            for (int p = 0; p < 4; ++p) w[p][e] = ws[p];
+          }
+#pragma unroll
+          for (int p = 0; p < 4; ++p)
+            sts128(a_tile_s + (uint32_t)p * a_bytes + soff[rr], make_uint4(w[p][0], w[p][1], w[p][2], w[p][3]));
+        } else {
+          float v[CHUNK];
+#pragma unroll
+          for (int e = 0; e < CHUNK; ++e) v[e] = 0.f;
+          if (live) {
+            const float qh = qhc[rr];
             const float4* src = reinterpret_cast<const float4*>(ra[rr] + ia);
 #pragma unroll
             for (int e4 = 0; e4 < CHUNK / 4; ++e4) {
@@ -440,158 +588,109 @@ __global__ void __launch_bounds__(kThreads, 1)
               v[4 * e4 + 2] = u.z * qh;
               v[4 * e4 + 3] = u.w * qh;
             }
-          } else {
-            // Khatri-Rao entry as an unevaluated pair (v + vl) from hi/lo factor
-            // copies: error-free products (FMA) keep it far below FP32 rounding
-            const float ql = qlc[rr];
-            float uh[CHUNK], ul[CHUNK];
-            if (a.ua_smem) {
+          }
+          float parts[NS][CHUNK];
 #pragma unroll
-              for (int e4 = 0; e4 < CHUNK / 4; ++e4) {
-                const float4 u = lds128(ua_row[rr] + (uint32_t)(ia + 4 * e4) * 4u);
-                uh[4 * e4 + 0] = u.x;
-                uh[4 * e4 + 1] = u.y;
-                uh[4 * e4 + 2] = u.z;
-                uh[4 * e4 + 3] = u.w;
-              }
-              // CHUNK (8) BF16 low parts in one 16-byte load
-              const float4 lraw = lds128(ua_rowl[rr] + (uint32_t)ia * 2u);
-              const uint32_t w4[4] = {__float_as_uint(lraw.x), __float_as_uint(lraw.y), __float_as_uint(lraw.z),
-                                      __float_as_uint(lraw.w)};
+          for (int e = 0; e < CHUNK; ++e) {
+            float p4[4];
+            split_value<Cfg>(v[e], p4);
 #pragma unroll
-              for (int k = 0; k < 4; ++k) {
-                ul[2 * k] = __uint_as_float(w4[k] << 16);
-                ul[2 * k + 1] = __uint_as_float(w4[k] & 0xffff0000u);
-              }
+            for (int p = 0; p < NS; ++p) parts[p][e] = p4[p];
+          }
+#pragma unroll
+          for (int p = 0; p < NS; ++p) {
+            uint4 w;
+            if constexpr (Cfg::kind == kKindTF32) {
+              w.x = __float_as_uint(parts[p][0]);
+              w.y = __float_as_uint(parts[p][1]);
+              w.z = __float_as_uint(parts[p][2]);
+              w.w = __float_as_uint(parts[p][3]);
             } else {
-              const float4* src = reinterpret_cast<const float4*>(ra[rr] + ia);
-              const float4* srcl = reinterpret_cast<const float4*>(ral[rr] + ia);
-#pragma unroll
-              for (int e4 = 0; e4 < CHUNK / 4; ++e4) {
-                const float4 u = __ldg(src + e4), l = __ldg(srcl + e4);
-                uh[4 * e4 + 0] = u.x;
-                uh[4 * e4 + 1] = u.y;
-                uh[4 * e4 + 2] = u.z;
-                uh[4 * e4 + 3] = u.w;
-                ul[4 * e4 + 0] = l.x;
-                ul[4 * e4 + 1] = l.y;
-                ul[4 * e4 + 2] = l.z;
-                ul[4 * e4 + 3] = l.w;
-              }
+              w.x = pack_bf16_exact(parts[p][0], parts[p][1]);
+              w.y = pack_bf16_exact(parts[p][2], parts[p][3]);
+              w.z = pack_bf16_exact(parts[p][4], parts[p][5]);
+              w.w = pack_bf16_exact(parts[p][6], parts[p][7]);
             }
-#pragma unroll
-            for (int k = 0; k < CHUNK; ++k) {
-              const float p = __fmul_rn(uh[k], qh);
-              v[k] = p;
-              vl[k] = __fadd_rn(__fmaf_rn(uh[k], qh, -p), __fmaf_rn(uh[k], ql, __fmul_rn(ul[k], qh)));
-            }
+            sts128(a_tile_s + (uint32_t)p * a_bytes + soff[rr], w);
           }
-        }
-        float parts[NS][CHUNK];
-#pragma unroll
-        for (int e = 0; e < CHUNK; ++e) {
-          float p4[4];
-          split_value<Cfg>(v[e], vl[e], rscale[rr], p4);
-#pragma unroll
-          for (int p = 0; p < NS; ++p) parts[p][e] = p4[p];
-        }
-#pragma unroll
-        for (int p = 0; p < NS; ++p) {
-          uint4 w;
-          if constexpr (Cfg::kind == kKindTF32) {
-            w.x = __float_as_uint(parts[p][0]);
-            w.y = __float_as_uint(parts[p][1]);
-            w.z = __float_as_uint(parts[p][2]);
-            w.w = __float_as_uint(parts[p][3]);
-          } else {
-            w.x = pack_bf16_exact(parts[p][0], parts[p][1]);
-            w.y = pack_bf16_exact(parts[p][2], parts[p][3]);
-            w.z = pack_bf16_exact(parts[p][4], parts[p][5]);
-            w.w = pack_bf16_exact(parts[p][6], parts[p][7]);
-          }
-          sts128(a_tile_s + (uint32_t)p * a_bytes + soff[rr], w);
         }
       }
       fence_async_shared();   // each writer: generic-proxy stores -> visible to the MMA
       __syncwarp();
-      if (lane == 0) mbar_arrive(&full_a[s]);
-      // advance this thread's column by BK: carry i_a into the remaining modes
+      if (lane == 0) mbar_arrive(&full[s]);
+      if (wrap) form_q(iq_n);
       jcur += BK;
-      ia += BK;
-      while (ia >= a.Ia_pad) {
-        ia -= a.Ia_pad;
-        qstale = true;
+      ia = ia_n;
 #pragma unroll
-        for (int t = 0; t < kMaxModes - 2; ++t) {
-          if (t < a.nq) {
-            if (++iq[t] < a.qdims[t]) break;
-            iq[t] = 0;
-          }
-        }
-      }
+      for (int t = 0; t < kMaxModes - 2; ++t) iq[t] = iq_n[t];
     }
 
+    }   // producers
+
+    if (warp >= kEpilogueWarp0) {
     // ---------------- epilogue: TMEM -> partial of Mbar_n ----------------------------
-    bool have = ok && nk > 0 && wait_bounded(accum, 0, abort_flag, a.err, 5);
+    // warps 5 and 9 share the MMA warp's scheduler: they sleep in the wait
+    bool have = ok && nk > 0 && wait_sleepy(accum, 0, abort_flag, a.err, 5);
     have = __all_sync(0xffffffffu, have);   // tcgen05.ld is warp-collective
     tc_fence_after();
-    const int quarter = warp & 3;                    // TMEM lanes 32*quarter .. +31
-    const int half = (warp - kProducerWarp0) >> 2;   // two warps per lane quarter split the columns
+    const int quarter = warp & 3;                      // TMEM lanes 32*quarter .. +31
+    const int grp = (warp - kEpilogueWarp0) >> 2;      // two warps per lane quarter split the columns
     const int m = quarter * 32 + lane;
     const int c = c0 + m;
     int Ec = 0;
     if constexpr (Cfg::exact) {
-      if (c < a.C) {
-        double b = (double)__ldg(a.cmax_a + c);
-#pragma unroll
-        for (int t = 0; t < kMaxModes - 2; ++t)
-          if (t < a.nq) b *= (double)__ldg(a.cmax_q[t] + c);
-        Ec = bound_exponent(b);
-      }
+      if (c < a.C) Ec = bound_exponent_prod(__ldg(a.cmax_a + c), a.cmax_q, a.nq, c);
     }
-    float* out = a.part + (int64_t)blockIdx.z * a.I * a.C;
     const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16);
-    for (int cc = 32 * half; cc < a.BN; cc += 64) {
-      const int width = (a.BN - cc >= 32) ? 32 : 16;
-      uint32_t v[32];
+    const uint32_t L = (uint32_t)a.lstride;
+    // 16-column slices (BN is a multiple of 16), dealt round-robin to the two
+    // warps of each lane quarter
+    for (int cc = 16 * grp; cc < a.BN; cc += 32) {
+      const uint32_t col = lane_base + (uint32_t)cc;
       if constexpr (!Cfg::exact) {
+        uint32_t v0[32], v1[32], v2[32];
         if (have) {
-          if (width == 32)
-            tmem_ld32(lane_base + (uint32_t)cc, v);
-          else
-            tmem_ld16(lane_base + (uint32_t)cc, v);
+          tmem_ld16(col, v0);
+          if (a.nlev > 1) tmem_ld16(col + L, v1);
+          if (a.nlev > 2) tmem_ld16(col + 2 * L, v2);
           tmem_ld_wait();
         }
+        float* out = a.part + (int64_t)blockIdx.z * a.I * a.C;
 #pragma unroll
-        for (int r = 0; r < 32; ++r) {
+        for (int r = 0; r < 16; ++r) {
           const int64_t i = (int64_t)n0 + cc + r;
-          if (r < width && i < a.I && c < a.C) out[i * a.C + c] = have ? __uint_as_float(v[r]) : 0.f;
+          if (i < a.I && c < a.C) {
+            float x = 0.f;
+            if (have) {
+              float lo = 0.f;   // the smaller levels first
+              if (a.nlev > 2) lo = __uint_as_float(v2[r]);
+              if (a.nlev > 1) lo += __uint_as_float(v1[r]);
+              x = __uint_as_float(v0[r]) + lo;
+            }
+            out[i * a.C + c] = x;
+          }
         }
       } else {
-        uint32_t v1[32], v2[32];
+        uint32_t v0[32], v1[32], v2[32], v3[32];
         if (have) {
-          if (width == 32) {
-            tmem_ld32(lane_base + (uint32_t)cc, v);
-            tmem_ld32(lane_base + (uint32_t)(a.acc_cols + cc), v1);
-            tmem_ld32(lane_base + (uint32_t)(2 * a.acc_cols + cc), v2);
-          } else {
-            tmem_ld16(lane_base + (uint32_t)cc, v);
-            tmem_ld16(lane_base + (uint32_t)(a.acc_cols + cc), v1);
-            tmem_ld16(lane_base + (uint32_t)(2 * a.acc_cols + cc), v2);
-          }
+          tmem_ld16(col, v0);
+          tmem_ld16(col + L, v1);
+          tmem_ld16(col + 2 * L, v2);
+          if (!a.merged) tmem_ld16(col + 3 * L, v3);
           tmem_ld_wait();
         }
-        // level 0 and level 1 are exact; add the three as an unevaluated FP32 pair
+        // levels 0 and 1 are exact; add the levels as an unevaluated FP32 pair
         // (hi, lo) with error-free TwoSum steps, scale by 2^(E_c + F_i - 14) and
         // store the pair; the consumer adds hi + lo
         float2* out2 = reinterpret_cast<float2*>(a.part) + (int64_t)blockIdx.z * a.I * a.C;
 #pragma unroll
-        for (int r = 0; r < 32; ++r) {
+        for (int r = 0; r < 16; ++r) {
           const int64_t i = (int64_t)n0 + cc + r;
-          if (r < width && i < a.I && c < a.C) {
+          if (i < a.I && c < a.C) {
             float2 val = make_float2(0.f, 0.f);
             if (have) {
-              const float l0 = __uint_as_float(v[r]), l1 = __uint_as_float(v1[r]), l2 = __uint_as_float(v2[r]);
+              const float l0 = __uint_as_float(v0[r]), l1 = __uint_as_float(v1[r]);
+              const float l2 = a.merged ? __uint_as_float(v2[r]) : __uint_as_float(v2[r]) + __uint_as_float(v3[r]);
               const float s = __fadd_rn(l0, l1);
               const float bb = __fsub_rn(s, l0);
               const float e1 = __fadd_rn(__fsub_rn(l0, __fsub_rn(s, bb)), __fsub_rn(l1, bb));
@@ -609,6 +708,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
       }
     }
+    }   // epilogue
   }
 
   tc_fence_before();
@@ -620,53 +720,28 @@ __global__ void __launch_bounds__(kThreads, 1)
 }
 
 // ---- precision forms -----------------------------------------------------------
+// nsplit parts per operand; the products of parts s, t with s + t < nsplit are
+// taken (TF32 / BF16: one; 3xTF32: hh, hl, lh; BF16x3: six; exact: ten).
 
 struct CfgTF32 {
-  static constexpr int kind = kKindTF32, fmt = 2, nsplit = 1, npass = 1, row_bytes = 128, elem = 4;
+  static constexpr int kind = kKindTF32, nsplit = 1, row_bytes = 128, elem = 4;
   static constexpr bool exact = false;
-  __device__ static constexpr int pass_a(int) { return 0; }
-  __device__ static constexpr int pass_b(int) { return 0; }
-  __device__ static constexpr int pass_acc(int) { return 0; }
-  __device__ static constexpr bool first_of_acc(int q) { return q == 0; }
 };
 struct Cfg3xTF32 {
-  // hi*hi + hi*lo + lo*hi
-  static constexpr int kind = kKindTF32, fmt = 2, nsplit = 2, npass = 3, row_bytes = 128, elem = 4;
+  static constexpr int kind = kKindTF32, nsplit = 2, row_bytes = 128, elem = 4;
   static constexpr bool exact = false;
-  __device__ static constexpr int pass_a(int q) { return q == 2 ? 1 : 0; }
-  __device__ static constexpr int pass_b(int q) { return q == 1 ? 1 : 0; }
-  __device__ static constexpr int pass_acc(int) { return 0; }
-  __device__ static constexpr bool first_of_acc(int q) { return q == 0; }
 };
 struct CfgBF16 {
-  static constexpr int kind = kKindBF16, fmt = 1, nsplit = 1, npass = 1, row_bytes = 128, elem = 2;
+  static constexpr int kind = kKindBF16, nsplit = 1, row_bytes = 128, elem = 2;
   static constexpr bool exact = false;
-  __device__ static constexpr int pass_a(int) { return 0; }
-  __device__ static constexpr int pass_b(int) { return 0; }
-  __device__ static constexpr int pass_acc(int) { return 0; }
-  __device__ static constexpr bool first_of_acc(int q) { return q == 0; }
 };
 struct CfgBF16x3 {
-  // (a, b) part pairs with a + b <= 2: hh, hm, mh, hl, lh, mm
-  static constexpr int kind = kKindBF16, fmt = 1, nsplit = 3, npass = 6, row_bytes = 128, elem = 2;
+  static constexpr int kind = kKindBF16, nsplit = 3, row_bytes = 128, elem = 2;
   static constexpr bool exact = false;
-  __device__ static constexpr int pass_a(int q) { return q == 2 ? 1 : q == 4 ? 2 : q == 5 ? 1 : 0; }
-  __device__ static constexpr int pass_b(int q) { return q == 1 ? 1 : q == 3 ? 2 : q == 5 ? 1 : 0; }
-  __device__ static constexpr int pass_acc(int) { return 0; }
-  __device__ static constexpr bool first_of_acc(int q) { return q == 0; }
 };
 struct CfgExact {
-  // slice pairs (s, t) with s + t <= 3; accumulators: level 0 | level 1 | levels 2-3
-  static constexpr int kind = kKindBF16, fmt = 1, nsplit = 4, npass = 10, row_bytes = 64, elem = 2;
+  static constexpr int kind = kKindBF16, nsplit = 4, row_bytes = 64, elem = 2;
   static constexpr bool exact = true;
-  __device__ static constexpr int pass_a(int q) {
-    return q == 2 ? 1 : q == 4 ? 1 : q == 5 ? 2 : q == 7 ? 1 : q == 8 ? 2 : q == 9 ? 3 : 0;
-  }
-  __device__ static constexpr int pass_b(int q) {
-    return q == 1 ? 1 : q == 3 ? 2 : q == 4 ? 1 : q == 6 ? 3 : q == 7 ? 2 : q == 8 ? 1 : 0;
-  }
-  __device__ static constexpr int pass_acc(int q) { return q == 0 ? 0 : (q <= 2 ? 1 : 2); }
-  __device__ static constexpr bool first_of_acc(int q) { return q == 0 || q == 1 || q == 3; }
 };
 
 template <class Cfg>
@@ -700,14 +775,51 @@ int form_elem_bytes(int precision) { return (precision == JKCALS_TF32 || precisi
 int form_bk(int precision) { return form_row_bytes(precision) / form_elem_bytes(precision); }
 int form_chunk(int precision) { return 16 / form_elem_bytes(precision); }
 int form_passes(int precision) {
-  switch (precision) {
-    case JKCALS_TF32: return CfgTF32::npass;
-    case JKCALS_3XTF32: return Cfg3xTF32::npass;
-    case JKCALS_BF16: return CfgBF16::npass;
-    case JKCALS_SPLIT_BF16: return CfgBF16x3::npass;
-    case JKCALS_EXACT_BF16: return CfgExact::npass;
-    default: return 0;
+  const int p = form_nsplit(precision);
+  return p * (p + 1) / 2;
+}
+
+int build_mma_list(int precision, TcPlan& p) {
+  const int P = p.nsplit;
+  const uint32_t fmt = (precision == JKCALS_TF32 || precision == JKCALS_3XTF32) ? 2u : 1u;   // TF32 : BF16
+  p.lstride = (p.BN + 31) / 32 * 32;
+  p.nlev = P;
+  p.merged = 0;
+  if (P * p.lstride > 512) {
+    // exact form with BN > 128: levels 2 and 3 share one accumulator
+    if (precision != JKCALS_EXACT_BF16 || 3 * p.lstride > 512) return JKCALS_ERR_UNSUPPORTED;
+    p.merged = 1;
   }
+  const int nacc = p.merged ? 3 : P;
+  p.tmem_cols = 32;
+  while (p.tmem_cols < nacc * p.lstride) p.tmem_cols *= 2;
+  // parts stack along N when each level starts right where the previous ends
+  const int G = (!p.merged && p.lstride == p.BN) ? 256 / p.BN : 1;
+  const uint32_t a_bytes = (uint32_t)kRowsM * p.row_bytes, b_bytes = (uint32_t)p.BN * p.row_bytes;
+  auto level = [&](int l) { return l > nacc - 1 ? nacc - 1 : l; };
+  MmaList& L = p.mma;
+  L.n = 0;
+  L.first = 0;
+  uint32_t started = 0;   // accumulators written by an earlier MMA of the list
+  for (int s = 0; s < P; ++s) {
+    for (int t0 = 0; t0 < P - s; t0 += G) {
+      const int t1 = (t0 + G - 1 < P - 1 - s) ? t0 + G - 1 : P - 1 - s;
+      const uint32_t N = (uint32_t)(t1 - t0 + 1) * (uint32_t)p.BN;
+      const int m = L.n++;
+      L.a[m] = ((uint32_t)s * a_bytes) >> 4;
+      L.b[m] = ((uint32_t)t0 * b_bytes) >> 4;
+      L.d[m] = (uint32_t)level(s + t0) * (uint32_t)p.lstride;
+      // FP32 accumulator, A/B formats, both K-major, N >> 3, M >> 4
+      L.idesc[m] = (1u << 4) | (fmt << 7) | (fmt << 10) | ((N >> 3) << 17) | ((uint32_t)(kRowsM >> 4) << 24);
+      // on the first K slice an MMA overwrites its columns iff none is started
+      bool fresh = true;
+      for (int t = t0; t <= t1; ++t)
+        if (started & (1u << level(s + t))) fresh = false;
+      if (fresh) L.first |= 1u << m;
+      for (int t = t0; t <= t1; ++t) started |= 1u << level(s + t);
+    }
+  }
+  return JKCALS_OK;
 }
 
 size_t tc_ua_bytes(const TcPlan& p) {
@@ -720,8 +832,8 @@ size_t tc_smem_bytes(const TcPlan& p) {
   const size_t row = (size_t)p.row_bytes;
   const size_t a_stage = (size_t)p.nsplit * kRowsM * row;
   const size_t b_stage = (size_t)p.nsplit * p.BN * row;
-  return 1024 /*alignment slack*/ + (size_t)p.stages_a * a_stage + (size_t)p.stages_b * b_stage + tc_ua_bytes(p) +
-         (2 * p.stages_a + 2 * p.stages_b + 1) * 8 + 16;
+  return 1024 /*alignment slack*/ + (size_t)p.stages * (a_stage + b_stage) + tc_ua_bytes(p) + (2 * p.stages + 1) * 8 +
+         16;
 }
 
 cudaError_t prepare_mttkrp_tc(int precision, size_t max_smem) {

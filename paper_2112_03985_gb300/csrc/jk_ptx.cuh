@@ -79,6 +79,36 @@ __device__ __forceinline__ bool wait_bounded(uint64_t* bar, uint32_t parity, vol
   }
 }
 
+// Bounded wait for threads that have nothing else to do: each try_wait may
+// suspend the thread in hardware for up to hint_ns (it resumes as soon as the
+// phase completes), so a waiting warp takes almost no issue slots from the
+// other warps of its scheduler.
+__device__ __forceinline__ bool mbar_try_wait_hint(uint64_t* bar, uint32_t parity, uint32_t hint_ns) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity), "r"(hint_ns)
+      : "memory");
+  return ok != 0;
+}
+
+__device__ __forceinline__ bool wait_sleepy(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int* err,
+                                            int code) {
+  const uint64_t t0 = global_ns();
+  while (true) {
+    if (mbar_try_wait_hint(bar, parity, 20000u)) return true;
+    if (*abort_flag) return false;
+    if (global_ns() - t0 > kWaitLimitNs) {
+      *abort_flag = 1;
+      atomicExch(err, code);
+      return false;
+    }
+  }
+}
+
 // Bounded wait that ignores the abort flag (used to drain own TMA copies).
 __device__ __forceinline__ void wait_drain(uint64_t* bar, uint32_t parity) {
   const uint64_t t0 = global_ns();

@@ -31,8 +31,8 @@ constexpr int kSliceBits = 7;
 struct TcArgs {
   int64_t I, Jp, kchunk;
   int C, BN, tmem_cols;
-  int stages_a, stages_b;          // A ring (Khatri-Rao tiles) and B ring (T tiles) depths
-  int acc_cols;                    // TMEM column stride between accumulators
+  int stages;                      // pipeline depth
+  int nlev, lstride, merged;       // accumulators in TMEM (see TcPlan)
   int Ia_pad;
   int64_t nkt;                     // k-steps per N tile in Tt
   const unsigned char* Tt;         // pre-tiled unfolding (layout above)
@@ -51,6 +51,7 @@ struct TcArgs {
   const int* rowexp;               // I_n: F_i of this mode's unfolding
   int ua_smem;                     // stage the 128 rows of UTa (and UTa_lo) in shared memory
   int ua_stride;                   // floats per staged FP32 row (BF16 low rows: Ia_pad elements)
+  MmaList mma;                     // MMAs per 32-byte K slice
 };
 
 int form_nsplit(int precision);
@@ -60,6 +61,10 @@ int form_elem_bytes(int precision);
 int form_chunk(int precision);
 int form_passes(int precision);
 size_t tc_smem_bytes(const TcPlan& p);
+// Accumulator layout and MMA list of a plan whose BN, nsplit and row_bytes are
+// set: levels s + t of the part products, B parts stacked along N where the
+// TMEM columns allow; JKCALS_ERR_UNSUPPORTED if the accumulators exceed TMEM.
+int build_mma_list(int precision, TcPlan& p);
 // Raise the kernel's dynamic shared-memory limit (call once, outside stream capture).
 cudaError_t prepare_mttkrp_tc(int precision, size_t max_smem);
 cudaError_t launch_mttkrp_tc(int precision, const TcPlan& p, const TcArgs& a, cudaStream_t s);
