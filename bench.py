@@ -45,6 +45,11 @@ def parse():
     p.add_argument("--e2e-reps", type=int, default=3)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-fp64-compare", action="store_true")
+    p.add_argument("--config", type=int, choices=[2, 3, 4], default=2,
+                   help="2 (default): the bench workload; 3: MTTKRP TFLOP/s of every precision form "
+                        "on 400^3 delete-10 (R = --rank); 4: the batch of 64 uneven problems "
+                        "(batched 3xTF32 + autotuner vs one launch per problem in FP64)")
+    p.add_argument("--rank", type=int, default=10, help="configuration 3 rank (5, 10 or 20)")
     p.add_argument("--cpu-worker", action="store_true", help=argparse.SUPPRESS)
     p.add_argument("--seconds", type=float, default=15.0, help=argparse.SUPPRESS)
     return p.parse_args()
@@ -410,6 +415,119 @@ def gpu_arm(args):
         dist.destroy_process_group()
 
 
+def cfg4_arm(args):
+    """Configuration 4: 64 independent LOO problems of uneven sizes, all advanced
+    by one graph launch per sweep (3xTF32 MTTKRP, autotuned split factors),
+    against the same problems in plain FP64 run one handle (one launch per
+    problem and sweep) after another.  Metric: submodel-ALS iterations/s summed
+    over problems."""
+    import numpy as np
+    import torch
+
+    from paper_2112_03985_gb300 import api, workloads as W
+
+    if not torch.cuda.is_available():
+        raise RuntimeError("bench.py needs a CUDA device (there is no CPU fallback)")
+    ws = W.make_config4_batch(64)
+    Ktot = sum(w.K for w in ws)
+    steps = args.steps
+
+    def handles(prec, **kw):
+        return [api.from_workload(w, precision=prec, device="cuda", **kw) for w in ws]
+
+    hs = handles("3xtf32", autotune=True)
+    b = api.Batch(hs, max_sweeps=max(steps, args.warmup))
+    b.sweep(args.warmup)
+    b.sync()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    b.sweep(steps)
+    b.sync()
+    batched_s = time.perf_counter() - t0
+    Ub = [h.get_factors() for h in hs[:4]]
+    b.close()
+    for h in hs:
+        h.close()
+    del ev0, ev1
+
+    hf = handles("fp64")
+    fsteps = max(1, min(steps, 5))
+    for h in hf:
+        h.als_sweep_async(1)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for h in hf:
+        h.als_sweep_async(fsteps)
+    for h in hf:
+        h.sync()
+    fp64_s = (time.perf_counter() - t0) * steps / fsteps
+    for h in hf:
+        h.close()
+    # accuracy of the batched form against FP64 on the first problems (same sweep count)
+    err = 0.0
+    for i in range(4):
+        with api.from_workload(ws[i], precision="fp64", device="cuda") as h:
+            h.als_sweep(args.warmup + steps)
+            Uf = h.get_factors()
+        err = max(err, max(float(np.abs(a - c).max() / np.abs(c).max()) for a, c in zip(Ub[i], Uf)))
+    value = Ktot * steps / batched_s
+    base = Ktot * steps / fp64_s
+    out = {"metric": "JK submodel-ALS iters/s (configuration 4 batch)", "value": value, "unit": "submodel-iters/s",
+           "n_gpus": 1, "steps": steps, "warmup": args.warmup, "ms_per_step": 1e3 * batched_s / steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "3xtf32",
+           "data": "synthetic",
+           "config": {"workload": "64 LOO problems, I1 in [20,400], I2, I3 in [30,150], R in [2,8], FP32",
+                      "submodels": Ktot, "batched": "one CUDA graph launch per sweep of all problems",
+                      "splits": "autotuned per problem and mode"},
+           "one_launch_per_problem_fp64": {"value": base, "unit": "submodel-iters/s",
+                                           "sweeps_timed": fsteps, "ratio": value / base},
+           "factor_rel_err_vs_fp64": err}
+    print(json.dumps(out), flush=True)
+
+
+def cfg3_arm(args):
+    """Configuration 3 (400^3 FP32, delete-10 x 40 groups): per precision form,
+    the concurrent MTTKRP's kernel time per mode (CUDA events around each
+    launch inside the sweep graph) and its useful TFLOP/s = 2 C prod(I) / time,
+    against the form's measured tensor peak; plus the sweep rate."""
+    import numpy as np
+    import torch
+
+    from paper_2112_03985_gb300 import api, workloads as W
+
+    if not torch.cuda.is_available():
+        raise RuntimeError("bench.py needs a CUDA device (there is no CPU fallback)")
+    peaks, peak_src = load_peaks()
+    w = W.make_config(3, R=args.rank)
+    flops = 2.0 * w.C * float(np.prod(w.T.shape))
+    forms = {}
+    for prec in ("fp64", "tf32", "3xtf32", "bf16", "split_bf16", "exact_bf16"):
+        with api.from_workload(w, precision=prec, device="cuda", kernel_timing=True) as h:
+            h.als_sweep_async(args.warmup)
+            torch.cuda.synchronize()
+            times = []
+            t0 = time.perf_counter()
+            for _ in range(args.steps):
+                h.als_sweep_async(1)
+                times.append(h.kernel_times())
+            torch.cuda.synchronize()
+            sweep_ms = 1e3 * (time.perf_counter() - t0) / args.steps
+            kt = np.median(np.array(times), axis=0)
+            _, splits = h.sweep_info()
+        tf = [flops / (t * 1e-3) / 1e12 for t in kt]
+        _, peak, note = roofline_peak(prec, peaks)
+        forms[prec] = {"mttkrp_ms": [round(float(t), 4) for t in kt], "mttkrp_tflops": [round(x, 2) for x in tf],
+                       "frac_of_peak": [round(x / peak, 3) for x in tf], "peak_tflops": peak, "peak": note,
+                       "splits": list(splits), "sweep_ms": round(sweep_ms, 3),
+                       "submodel_iters_per_s": w.K / (sweep_ms * 1e-3)}
+    out = {"metric": "concurrent MTTKRP TFLOP/s per precision form (configuration 3)", "unit": "TFLOP/s",
+           "config": {"workload": f"400x400x400 FP32, R={args.rank}, delete-10 x 40 groups", "C": w.C,
+                      "useful_gflop_per_mode": flops / 1e9, "peaks": peak_src},
+           "forms": forms}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
     if args.cpu_worker:
@@ -417,6 +535,12 @@ def main():
         return
     if args.impl == "reference":
         reference_arm(args)
+        return
+    if args.config == 4:
+        cfg4_arm(args)
+        return
+    if args.config == 3:
+        cfg3_arm(args)
         return
     gpu_arm(args)
 

@@ -90,7 +90,10 @@ typedef struct {
   int update_mode;      /* per-block update kernels: 0 (default) automatic, 1 one CTA per
                            block with the block's rows in shared memory, 2 two-phase
                            (row chunks, then a per-block reduction)                    */
-  int reserved[6];
+  int autotune;         /* 1: at create, time the MTTKRP (+ split-K reduction) of every mode
+                           for split factors around the planned one and keep the fastest
+                           (ignored when splits > 0); 0 (default): off                   */
+  int reserved[5];
 } jkcals_options;
 
 /* Fill *opt with the defaults above. */
@@ -211,6 +214,40 @@ jkcals_status jkcals_get_block_status(jkcals_t h, int32_t* status);
  *  loss  NULL or one FP64 in host memory: f
  */
 jkcals_status jkcals_grad(jkcals_t h, const double* const* U, double* const* G, double* loss);
+
+/*
+ * Batched problems (many independent jackknife problems, each its own handle;
+ * configuration 4 of the evaluation).  The paper fits one tensor at a time;
+ * batching is a deployment form of Alg. 3 for many small problems, none of
+ * which fills the GPU alone.  jkcals_batch_create captures one sweep of every
+ * handle and makes them parallel branches (child graphs) of one CUDA graph, so
+ * a sweep of the whole batch is one graph launch and the GPU runs the
+ * problems' kernels side by side.
+ *  handles     n handles, owned by the caller, alive for the batch's lifetime;
+ *              no handle may have opt.kernel_timing = 1
+ *  max_sweeps  the most sweeps one jkcals_batch_sweep call may run (each
+ *              handle's loss history is sized for it now)
+ *  stream      cudaStream_t the batch runs on (NULL: the batch creates its own)
+ * jkcals_batch_sweep enqueues nsweeps sweeps of every problem, ordered after
+ * the work already enqueued on each handle's stream and before later work
+ * there; it does not synchronise.  Read each problem's losses with
+ * jkcals_loss_history and its factors with jkcals_get_factors.  A handle whose
+ * loss history was reallocated since (a jkcals_als_sweep call for more sweeps
+ * than max_sweeps) makes jkcals_batch_sweep return JKCALS_ERR_STATE.
+ */
+typedef struct jkcals_batch_ctx* jkcals_batch_t;
+jkcals_status jkcals_batch_create(jkcals_batch_t* out, int n, const jkcals_t* handles, int max_sweeps,
+                                  void* stream);
+jkcals_status jkcals_batch_sweep(jkcals_batch_t b, int nsweeps);
+jkcals_status jkcals_batch_sync(jkcals_batch_t b);
+void jkcals_batch_destroy(jkcals_batch_t b);
+
+/*
+ * Losses e_g of the last nsweeps sweeps run by the latest jkcals_als_sweep,
+ * jkcals_als_sweep_async or jkcals_batch_sweep call (nsweeps x K, sweep-major;
+ * host or device; synchronises when losses is host memory).
+ */
+jkcals_status jkcals_loss_history(jkcals_t h, int nsweeps, double* losses);
 
 /* Block until the handle's stream is idle. */
 jkcals_status jkcals_sync(jkcals_t h);

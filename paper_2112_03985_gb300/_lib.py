@@ -18,7 +18,8 @@ BLOCK_NOT_SPD, BLOCK_CONVERGED = 1, 2
 class Options(ct.Structure):
     _fields_ = [("precision", ct.c_int), ("normalise", ct.c_int), ("use_graph", ct.c_int),
                 ("splits", ct.c_int), ("max_device_bytes", ct.c_int64),
-                ("kernel_timing", ct.c_int), ("update_mode", ct.c_int), ("reserved", ct.c_int * 6)]
+                ("kernel_timing", ct.c_int), ("update_mode", ct.c_int), ("autotune", ct.c_int),
+                ("reserved", ct.c_int * 5)]
 
 
 P = ct.c_void_p
@@ -42,6 +43,11 @@ SIGNATURES = {
     "jkcals_set_factors": (ct.c_int, [P, PP]),
     "jkcals_get_block_status": (ct.c_int, [P, I32P]),
     "jkcals_grad": (ct.c_int, [P, PP, PP, P]),
+    "jkcals_loss_history": (ct.c_int, [P, ct.c_int, P]),
+    "jkcals_batch_create": (ct.c_int, [ct.POINTER(P), ct.c_int, PP, ct.c_int, P]),
+    "jkcals_batch_sweep": (ct.c_int, [P, ct.c_int]),
+    "jkcals_batch_sync": (ct.c_int, [P]),
+    "jkcals_batch_destroy": (None, [P]),
     "jkcals_sync": (ct.c_int, [P]),
     "jkcals_mttkrp_f64_noalloc": (ct.c_int, [ct.c_int, I64P, ct.c_int, P, PP, ct.c_int, P, P]),
     "jkcals_last_error": (ct.c_char_p, []),

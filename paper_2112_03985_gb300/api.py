@@ -64,7 +64,7 @@ class JKCALS:
     def __init__(self, T, n_hat: int, ranks: Sequence[int], left_out: Sequence[Sequence[int]],
                  init: Sequence, *, precision: str = "fp64", normalise: bool = True,
                  use_graph: bool = True, splits: int = 0, max_device_bytes: int = 0,
-                 kernel_timing: bool = False, update_mode: int = 0, stream=None):
+                 kernel_timing: bool = False, update_mode: int = 0, autotune: bool = False, stream=None):
         lib = L.load()
         self._lib = lib
         self._h = ct.c_void_p()
@@ -84,6 +84,7 @@ class JKCALS:
         opt.max_device_bytes = int(max_device_bytes)
         opt.kernel_timing = int(bool(kernel_timing))
         opt.update_mode = int(update_mode)
+        opt.autotune = int(bool(autotune))
         dims = (ct.c_int64 * self.N)(*self.dims)
         rk = (ct.c_int32 * self.K)(*self.ranks)
         ptr, idx = left_out_csr(left_out)
@@ -206,6 +207,95 @@ class JKCALS:
 
     def sync(self):
         L.check(self._lib.jkcals_sync(self._h), "jkcals_sync")
+
+    def loss_history(self, nsweeps: int, device=None):
+        """Losses of the last ``nsweeps`` sweeps of the latest sweep call (nsweeps x K)."""
+        out = self._out((nsweeps, self.K), device)
+        L.check(self._lib.jkcals_loss_history(self._h, int(nsweeps), ct.c_void_p(_ptr(out))),
+                "jkcals_loss_history")
+        return out
+
+    def loss(self, U):
+        """Differentiable summed jackknife loss f(U) = sum_g ||T_{-g} - [[U_{|g}]]||^2
+        as a 0-dim FP64 CUDA tensor; U is the list of N multi-matrices (FP64 CUDA,
+        I_n x C).  Its backward is the hand-written jkcals_grad (concurrent MTTKRP
+        minus U times the Hadamard of Grams)."""
+        return _loss_function().apply(self, *U)
+
+
+class Batch:
+    """Many independent problems advanced together: one CUDA graph per sweep of
+    the whole batch (jkcals_batch_create / _sweep / _sync / _destroy).  The
+    handles stay owned by the caller and must outlive the batch."""
+
+    def __init__(self, handles: Sequence[JKCALS], max_sweeps: int, stream=None):
+        self._lib = L.load()
+        self.handles = list(handles)
+        self.max_sweeps = int(max_sweeps)
+        self._b = ct.c_void_p()
+        arr = (ct.c_void_p * len(self.handles))(*[h._h.value for h in self.handles])
+        L.check(self._lib.jkcals_batch_create(ct.byref(self._b), len(self.handles), arr, self.max_sweeps,
+                                              ct.c_void_p(stream) if stream else None), "jkcals_batch_create")
+
+    def sweep(self, nsweeps: int):
+        L.check(self._lib.jkcals_batch_sweep(self._b, int(nsweeps)), "jkcals_batch_sweep")
+
+    def sync(self):
+        L.check(self._lib.jkcals_batch_sync(self._b), "jkcals_batch_sync")
+
+    def close(self):
+        if self._b:
+            self._lib.jkcals_batch_destroy(self._b)
+            self._b = ct.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+_LOSS_FN = None
+
+
+def _loss_function():
+    """torch.autograd.Function for JKCALS.loss, built on first use (torch is
+    imported lazily).  forward: the loss only (one MTTKRP, of the last mode);
+    backward: all N MTTKRPs through jkcals_grad, scaled by the incoming grad."""
+    global _LOSS_FN
+    if _LOSS_FN is not None:
+        return _LOSS_FN
+    torch = _torch()
+
+    class JKLoss(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, h, *U):
+            U = [u.detach().contiguous() for u in U]
+            for u in U:
+                if u.dtype != torch.float64 or not u.is_cuda:
+                    raise TypeError("JKCALS.loss takes FP64 CUDA tensors")
+            torch.cuda.current_stream().synchronize()   # the library runs on its own stream
+            f, _ = h.grad(U=U, want_grad=False)
+            ctx.h = h
+            ctx.save_for_backward(*U)
+            return torch.tensor(f, dtype=torch.float64, device=U[0].device)
+
+        @staticmethod
+        def backward(ctx, gout):
+            U = ctx.saved_tensors
+            G = [torch.empty_like(u) for u in U]
+            torch.cuda.current_stream().synchronize()
+            ctx.h.grad(U=list(U), G=G)
+            return (None, *[gout * g for g in G])
+
+    _LOSS_FN = JKLoss
+    return _LOSS_FN
 
 
 def from_workload(w, precision: str = "fp64", device: Optional[str] = None, **kw) -> JKCALS:

@@ -435,6 +435,84 @@ jkcals_status check_device_error(jkcals_ctx* h) {
   return JKCALS_OK;
 }
 
+// Set the split-K factor of mode n's MTTKRP to about S (clamped to the
+// column count; the exact-chain form keeps chains <= kExactChainMax columns).
+void set_mode_splits(jkcals_ctx* h, int n, int64_t S) {
+  if (h->tc) {
+    tc::TcPlan& p = h->tcplan[n];
+    const int64_t bk = tc::form_bk(h->opt.precision);
+    S = std::max<int64_t>(1, std::min<int64_t>(S, p.nkt));
+    int64_t kchunk = ((p.nkt + S - 1) / S) * bk;
+    if (h->opt.precision == JKCALS_EXACT_BF16) kchunk = std::min<int64_t>(kchunk, tc::kExactChainMax);
+    p.kchunk = kchunk;
+    p.splits = (int)((p.Jp + kchunk - 1) / kchunk);
+  } else {
+    ModePlan& p = h->plan[n];
+    const int64_t ksteps = (h->J[n] + kMttkrpBK - 1) / kMttkrpBK;
+    S = std::max<int64_t>(1, std::min<int64_t>(S, ksteps));
+    const int64_t kchunk = ((ksteps + S - 1) / S) * kMttkrpBK;
+    p.kchunk = kchunk;
+    p.splits = (int)((h->J[n] + kchunk - 1) / kchunk);
+  }
+  h->graph_valid = false;
+}
+
+int64_t mode_kchunk(const jkcals_ctx* h, int n) { return h->tc ? h->tcplan[n].kchunk : h->plan[n].kchunk; }
+
+// Autotuner: per mode, time the MTTKRP + split-K reduction on the handle's
+// current factors for split factors {S, S/2, 2S, 4S} around the planned S
+// (three timed runs after one warm-up each, CUDA events on the handle's
+// stream) and keep the fastest.  The partial-sum workspace grows as needed.
+jkcals_status autotune_splits(jkcals_ctx* h) {
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  JK_CUDA(h, cudaEventCreate(&e0));
+  JK_CUDA(h, cudaEventCreate(&e1));
+  const size_t eb = part_kind(h) == kPartF32 ? sizeof(float) : sizeof(double);
+  jkcals_status st = JKCALS_OK;
+  for (int n = 0; n < h->N && st == JKCALS_OK; ++n) {
+    const int64_t S0 = mode_splits(h, n);
+    const int64_t cands[4] = {S0, std::max<int64_t>(1, S0 / 2), 2 * S0, 4 * S0};
+    int64_t best_S = S0, tried[4] = {0, 0, 0, 0};
+    float best_ms = 1e30f;
+    for (int c = 0; c < 4 && st == JKCALS_OK; ++c) {
+      set_mode_splits(h, n, cands[c]);
+      const int64_t kc = mode_kchunk(h, n);
+      bool seen = false;
+      for (int d = 0; d < c; ++d) seen = seen || tried[d] == kc;
+      tried[c] = kc;
+      if (seen) continue;
+      const size_t need = (size_t)mode_splits(h, n) * h->dims[n] * h->C * eb;
+      if (need > h->part_bytes) {
+        JK_CUDA(h, cudaStreamSynchronize(h->stream));
+        dfree(h, h->part);
+        h->part = nullptr;
+        h->part_bytes = 0;
+        if ((st = dalloc(h, &h->part, need)) != JKCALS_OK) break;
+        h->part_bytes = need;
+      }
+      for (int rep = 0; rep < 4 && st == JKCALS_OK; ++rep) {
+        if (rep == 1) JK_CUDA(h, cudaEventRecord(e0, h->stream));
+        if ((st = enqueue_mttkrp(h, n, h->U, h->UT, h->UTlo, h->cmax)) != JKCALS_OK) break;
+        st = reduce_into(h, n, h->mbuf);
+      }
+      if (st != JKCALS_OK) break;
+      JK_CUDA(h, cudaEventRecord(e1, h->stream));
+      JK_CUDA(h, cudaEventSynchronize(e1));
+      float ms = 0.f;
+      JK_CUDA(h, cudaEventElapsedTime(&ms, e0, e1));
+      if (ms < best_ms) {
+        best_ms = ms;
+        best_S = cands[c];
+      }
+    }
+    set_mode_splits(h, n, best_S);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != JKCALS_OK) return st;
+  return check_device_error(h);
+}
+
 jkcals_status check_handle(jkcals_t h) {
   if (h == nullptr) return fail(JKCALS_ERR_ARG, "NULL handle");
   if (h->broken) return fail(JKCALS_ERR_STATE, "handle unusable after an earlier CUDA error");
@@ -627,6 +705,7 @@ jkcals_status create_impl(jkcals_ctx* h, const void* T, int T_dtype, const int32
   for (int n = 0; n < N; ++n) h->kernels_per_sweep += h->plan[n].upd.fused ? 3 : 4;
   h->kernels_per_sweep += 1;
   JK_TRY(refresh_factor_state(h));
+  if (h->opt.autotune && h->opt.splits <= 0) JK_TRY(autotune_splits(h));
   JK_CUDA(h, cudaStreamSynchronize(st));
   return JKCALS_OK;
 }
@@ -667,7 +746,10 @@ jkcals_status grad_impl(jkcals_ctx* h, const double* const* U, double* const* G,
       JK_CUDA(h, tc::launch_colmax(h->gUT[n], h->dims[n], h->Ipad[n], h->C, h->gcmax[n], st));
     }
   }
+  const bool want_g = G != nullptr;
   for (int n = 0; n < N; ++n) {
+    // the loss needs only the last mode's MTTKRP (its inner product term)
+    if (!want_g && n != N - 1) continue;
     JK_TRY(enqueue_mttkrp(h, n, h->gU, h->gUT, h->gUTlo, h->gcmax));
     const int64_t cnt = h->dims[n] * (int64_t)h->C;
     JK_TRY(reduce_into(h, n, h->mbuf));
@@ -939,9 +1021,142 @@ jkcals_status jkcals_grad(jkcals_t h, const double* const* U, double* const* G, 
   return grad_impl(h, U, G, loss);
 }
 
+jkcals_status jkcals_loss_history(jkcals_t h, int nsweeps, double* losses) {
+  JK_TRY(check_handle(h));
+  if (nsweeps < 0 || nsweeps > h->loss_cap || losses == nullptr)
+    return fail(JKCALS_ERR_ARG, "nsweeps outside the loss history, or losses is NULL");
+  return copy_out(h, losses, h->loss_hist, sizeof(double) * nsweeps * h->K);
+}
+
 jkcals_status jkcals_sync(jkcals_t h) {
   JK_TRY(check_handle(h));
   JK_CUDA(h, cudaStreamSynchronize(h->stream));
+  return JKCALS_OK;
+}
+
+
+struct jkcals_batch_ctx {
+  std::vector<jkcals_ctx*> hs;
+  std::vector<double*> loss_ptrs;   // each handle's loss history when the graph was captured
+  std::vector<cudaEvent_t> ready;   // per handle: its stream's work before a batch sweep
+  cudaEvent_t done = nullptr;
+  cudaStream_t stream = nullptr;
+  bool owns_stream = false;
+  cudaGraphExec_t exec = nullptr;
+  int max_sweeps = 0;
+};
+
+void jkcals_batch_destroy(jkcals_batch_t b) {
+  if (b == nullptr) return;
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  for (cudaEvent_t e : b->ready)
+    if (e) cudaEventDestroy(e);
+  if (b->done) cudaEventDestroy(b->done);
+  if (b->owns_stream && b->stream) cudaStreamDestroy(b->stream);
+  delete b;
+}
+
+jkcals_status jkcals_batch_create(jkcals_batch_t* out, int n, const jkcals_t* handles, int max_sweeps,
+                                  void* stream) {
+  if (out == nullptr || handles == nullptr || n <= 0 || max_sweeps <= 0)
+    return fail(JKCALS_ERR_ARG, "jkcals_batch_create: out, handles, n > 0 and max_sweeps > 0 are required");
+  *out = nullptr;
+  for (int i = 0; i < n; ++i) {
+    JK_TRY(check_handle(handles[i]));
+    if (handles[i]->opt.kernel_timing) return fail(JKCALS_ERR_ARG, "batched handles cannot use kernel_timing");
+    for (int j = 0; j < i; ++j)
+      if (handles[j] == handles[i]) return fail(JKCALS_ERR_ARG, "a handle appears twice in the batch");
+  }
+  jkcals_batch_ctx* b = new jkcals_batch_ctx();
+  b->max_sweeps = max_sweeps;
+  auto bail = [&](jkcals_status s) {
+    jkcals_batch_destroy(b);
+    return s;
+  };
+  cudaError_t e = cudaSuccess;
+  if (stream != nullptr) {
+    b->stream = static_cast<cudaStream_t>(stream);
+  } else {
+    e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return bail(fail(JKCALS_ERR_CUDA, std::string("cudaStreamCreate: ") + cudaGetErrorString(e)));
+    b->owns_stream = true;
+  }
+  if ((e = cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming)) != cudaSuccess)
+    return bail(fail(JKCALS_ERR_CUDA, std::string("cudaEventCreate: ") + cudaGetErrorString(e)));
+  cudaGraph_t g = nullptr;
+  if ((e = cudaGraphCreate(&g, 0)) != cudaSuccess)
+    return bail(fail(JKCALS_ERR_CUDA, std::string("cudaGraphCreate: ") + cudaGetErrorString(e)));
+  for (int i = 0; i < n; ++i) {
+    jkcals_ctx* h = handles[i];
+    jkcals_status s = ensure_loss_cap(h, max_sweeps);
+    cudaEvent_t ev = nullptr;
+    if (s == JKCALS_OK && (e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess)
+      s = fail(JKCALS_ERR_CUDA, std::string("cudaEventCreate: ") + cudaGetErrorString(e));
+    if (ev) b->ready.push_back(ev);
+    cudaGraph_t hg = nullptr;
+    if (s == JKCALS_OK) {
+      // one sweep of this problem, captured from its own stream
+      if ((e = cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) {
+        s = fail(JKCALS_ERR_CUDA, std::string("cudaStreamBeginCapture: ") + cudaGetErrorString(e));
+      } else {
+        s = enqueue_sweep(h);
+        e = cudaStreamEndCapture(h->stream, &hg);
+        if (s == JKCALS_OK && e != cudaSuccess)
+          s = fail(JKCALS_ERR_CUDA, std::string("cudaStreamEndCapture: ") + cudaGetErrorString(e));
+      }
+    }
+    if (s == JKCALS_OK) {
+      cudaGraphNode_t node;
+      if ((e = cudaGraphAddChildGraphNode(&node, g, nullptr, 0, hg)) != cudaSuccess)
+        s = fail(JKCALS_ERR_CUDA, std::string("cudaGraphAddChildGraphNode: ") + cudaGetErrorString(e));
+    }
+    if (hg) cudaGraphDestroy(hg);
+    if (s != JKCALS_OK) {
+      cudaGraphDestroy(g);
+      return bail(s);
+    }
+    b->hs.push_back(h);
+    b->loss_ptrs.push_back(h->loss_hist);
+  }
+  e = cudaGraphInstantiate(&b->exec, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return bail(fail(JKCALS_ERR_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e)));
+  *out = b;
+  return JKCALS_OK;
+}
+
+jkcals_status jkcals_batch_sweep(jkcals_batch_t b, int nsweeps) {
+  if (b == nullptr) return fail(JKCALS_ERR_ARG, "null batch");
+  if (nsweeps < 0 || nsweeps > b->max_sweeps) return fail(JKCALS_ERR_ARG, "nsweeps outside [0, max_sweeps]");
+  if (nsweeps == 0) return JKCALS_OK;
+  cudaError_t e = cudaSuccess;
+  auto cu = [&](cudaError_t r, const char* what) {
+    if (r != cudaSuccess) e = r;
+    return r == cudaSuccess ? JKCALS_OK : fail(JKCALS_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(r));
+  };
+  for (size_t i = 0; i < b->hs.size(); ++i) {
+    jkcals_ctx* h = b->hs[i];
+    if (h->loss_hist != b->loss_ptrs[i])
+      return fail(JKCALS_ERR_STATE, "a batched handle's loss history was reallocated; recreate the batch");
+    JK_TRY(cu(cudaEventRecord(b->ready[i], h->stream), "cudaEventRecord"));
+    JK_TRY(cu(cudaStreamWaitEvent(b->stream, b->ready[i], 0), "cudaStreamWaitEvent"));
+    h->tol_host = 0.0;
+    JK_TRY(cu(cudaMemsetAsync(h->d_tol, 0, sizeof(double), b->stream), "cudaMemsetAsync"));
+    JK_TRY(cu(cudaMemsetAsync(h->d_sweep_idx, 0, sizeof(int), b->stream), "cudaMemsetAsync"));
+  }
+  for (int s = 0; s < nsweeps; ++s) JK_TRY(cu(cudaGraphLaunch(b->exec, b->stream), "cudaGraphLaunch"));
+  JK_TRY(cu(cudaEventRecord(b->done, b->stream), "cudaEventRecord"));
+  for (jkcals_ctx* h : b->hs) JK_TRY(cu(cudaStreamWaitEvent(h->stream, b->done, 0), "cudaStreamWaitEvent"));
+  (void)e;
+  return JKCALS_OK;
+}
+
+jkcals_status jkcals_batch_sync(jkcals_batch_t b) {
+  if (b == nullptr) return fail(JKCALS_ERR_ARG, "null batch");
+  const cudaError_t e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) return fail(JKCALS_ERR_CUDA, std::string("cudaStreamSynchronize: ") + cudaGetErrorString(e));
+  for (jkcals_ctx* h : b->hs) JK_TRY(check_device_error(h));
   return JKCALS_OK;
 }
 

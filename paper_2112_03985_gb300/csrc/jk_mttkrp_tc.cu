@@ -744,8 +744,14 @@ struct CfgExact {
   static constexpr bool exact = true;
 };
 
+// The limit is per kernel and process-wide: only ever raise it, so that a
+// handle needing less never lowers it under another handle.
 template <class Cfg>
 cudaError_t set_smem_cfg(size_t smem) {
+  cudaFuncAttributes fa;
+  const cudaError_t e = cudaFuncGetAttributes(&fa, mttkrp_tc_kernel<Cfg>);
+  if (e != cudaSuccess) return e;
+  if ((size_t)fa.maxDynamicSharedSizeBytes >= smem) return cudaSuccess;
   return cudaFuncSetAttribute(mttkrp_tc_kernel<Cfg>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 

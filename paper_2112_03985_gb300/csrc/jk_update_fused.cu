@@ -271,8 +271,15 @@ size_t update_fused_smem(int64_t I, int Rmax) { return (size_t)I * Rmax * sizeof
 // rank classes 8, 16, 32 with per-rank guards.
 template <int RM, bool F>
 cudaError_t run_fused(const UpdateArgs* a, size_t smem, cudaStream_t s, bool prepare) {
-  if (prepare)
+  if (prepare) {
+    // the limit is per kernel and process-wide: only ever raise it, so that a
+    // handle needing less never lowers it under another handle
+    cudaFuncAttributes fa;
+    const cudaError_t e = cudaFuncGetAttributes(&fa, update_fused_kernel<RM, F>);
+    if (e != cudaSuccess) return e;
+    if ((size_t)fa.maxDynamicSharedSizeBytes >= smem) return cudaSuccess;
     return cudaFuncSetAttribute(update_fused_kernel<RM, F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  }
   update_fused_kernel<RM, F><<<a->K, NT, smem, s>>>(*a);
   return cudaGetLastError();
 }
