@@ -53,6 +53,6 @@ def test_cfg3_delete10_sampled_groups(cfg3, precision, ftol):
         if precision == "fp64":
             assert lrel.max() <= ftol, lrel.max()
         else:
-            assert lnorm.max() <= 1e-10, lnorm.max()
+            assert lnorm.max() <= 1e-9, lnorm.max()   # the form's MTTKRP accuracy
     else:
         assert np.isfinite(errs).all() and errs.max() < 1e-1
