@@ -117,3 +117,40 @@ def test_tc_gradient_matches_oracle():
     for n in range(4):
         err = np.linalg.norm(G[n] - G_ref[n]) / np.linalg.norm(G_ref[n])
         assert err <= 1e-4, (n, err)
+
+
+def test_jackknife_se_error_per_form_cfg2():
+    """Configuration 2, 100 sweeps: factor and jackknife standard-error (Alg. 2
+    std line, modes != n_hat) relative errors of every precision form against
+    the FP64 path (itself matched to the oracle on sampled blocks).  Each
+    submodel is aligned (Alg. 2 adjustment line) to submodel 0 of the FP64 run."""
+    _cuda()
+    w = W.make_config(2)
+    offs = offsets(w.ranks)
+
+    def fit(prec):
+        with api.from_workload(w, precision=prec, device="cuda") as h:
+            h.als_sweep(w.sweeps)
+            return h.get_factors()
+
+    def se(U, ref):
+        est = []
+        for g in range(w.K):
+            Ug = [u[:, offs[g]:offs[g + 1]] for u in U]
+            A = O.align_to_reference(Ug, ref, w.n_hat)
+            est.append(np.concatenate([A[k].ravel() for k in range(3) if k != w.n_hat]))
+        return O.jackknife_se(np.asarray(est))
+
+    U64 = fit("fp64")
+    ref = [u[:, offs[0]:offs[1]] for u in U64]
+    se64 = se(U64, ref)
+    report = {}
+    for prec in ("exact_bf16", "3xtf32", "split_bf16", "tf32", "bf16"):
+        U = fit(prec)
+        ferr = max(float(np.abs(a - b).max() / np.abs(b).max()) for a, b in zip(U, U64))
+        serr = float(np.abs(se(U, ref) - se64).max() / np.abs(se64).max())
+        report[prec] = (ferr, serr)
+    print("\ncfg2 100 sweeps, vs FP64: " + ", ".join(f"{p}: factors {f:.1e} SE {s:.1e}" for p, (f, s) in report.items()))
+    assert report["exact_bf16"][0] <= 1e-6 and report["exact_bf16"][1] <= 1e-6
+    for p, (f, s) in report.items():
+        assert np.isfinite(f) and np.isfinite(s)
