@@ -385,37 +385,52 @@ __global__ void __launch_bounds__(kThreads, 1) mttkrp_tc_kernel(const TcArgs a) 
     }
     if (a.ua_smem) {
       // stage the CTA's 128 factor rows of mode a once (FP32 hi; BF16 lo for
-      // the exact-chain form, which keeps the pair to ~2^-32): the k loop then
-      // reads them from shared memory instead of L2
-      const int ptid = pw * 32 + lane;
+      // the exact form; zero past C): the k loop then reads them from shared
+      // memory instead of L2
+      constexpr int kStagers = 32 * kProducerWarps;
+      constexpr int kU = 4;   // loads in flight per thread
+      const int tid = pw * 32 + lane;
       const int n4 = a.Ia_pad / 4;
-      const int total = kRowsM * n4;
-      constexpr int kU = 2;   // loads in flight per thread
-      for (int idx0 = ptid; idx0 < total; idx0 += kU * 32 * kProducerWarps) {
-        float4 hv[kU], lv[kU];
+      for (int idx0 = tid; idx0 < kRowsM * n4; idx0 += kU * kStagers) {
+        float4 v[kU];
 #pragma unroll
         for (int u = 0; u < kU; ++u) {
-          const int idx = idx0 + u * 32 * kProducerWarps;
+          const int idx = idx0 + u * kStagers;
           const int row = idx / n4, col = (idx - row * n4) * 4;
-          const int c = c0 + row;
-          hv[u] = lv[u] = make_float4(0.f, 0.f, 0.f, 0.f);
-          if (idx < total && c < a.C) {
-            hv[u] = __ldg(reinterpret_cast<const float4*>(a.UTa + (int64_t)c * a.Ia_pad + col));
-            if constexpr (Cfg::exact)
-              lv[u] = __ldg(reinterpret_cast<const float4*>(a.UTa_lo + (int64_t)c * a.Ia_pad + col));
-          }
+          v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (idx < kRowsM * n4 && c0 + row < a.C)
+            v[u] = __ldg(reinterpret_cast<const float4*>(a.UTa + (int64_t)(c0 + row) * a.Ia_pad + col));
         }
 #pragma unroll
         for (int u = 0; u < kU; ++u) {
-          const int idx = idx0 + u * 32 * kProducerWarps;
-          if (idx < total) {
+          const int idx = idx0 + u * kStagers;
+          if (idx < kRowsM * n4) {
             const int row = idx / n4, col = (idx - row * n4) * 4;
             sts128(smem_u32(ua_hi + (size_t)row * a.ua_stride + col),
-                   make_uint4(__float_as_uint(hv[u].x), __float_as_uint(hv[u].y), __float_as_uint(hv[u].z),
-                              __float_as_uint(hv[u].w)));
-            if constexpr (Cfg::exact) {
-              const __nv_bfloat162 l01 = __floats2bfloat162_rn(lv[u].x, lv[u].y);
-              const __nv_bfloat162 l23 = __floats2bfloat162_rn(lv[u].z, lv[u].w);
+                   make_uint4(__float_as_uint(v[u].x), __float_as_uint(v[u].y), __float_as_uint(v[u].z),
+                              __float_as_uint(v[u].w)));
+          }
+        }
+      }
+      if constexpr (Cfg::exact) {
+        // FP32 low parts rounded to BF16 (the pair then holds U to ~2^-32)
+        for (int idx0 = tid; idx0 < kRowsM * n4; idx0 += kU * kStagers) {
+          float4 v[kU];
+#pragma unroll
+          for (int u = 0; u < kU; ++u) {
+            const int idx = idx0 + u * kStagers;
+            const int row = idx / n4, col = (idx - row * n4) * 4;
+            v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (idx < kRowsM * n4 && c0 + row < a.C)
+              v[u] = __ldg(reinterpret_cast<const float4*>(a.UTa_lo + (int64_t)(c0 + row) * a.Ia_pad + col));
+          }
+#pragma unroll
+          for (int u = 0; u < kU; ++u) {
+            const int idx = idx0 + u * kStagers;
+            if (idx < kRowsM * n4) {
+              const int row = idx / n4, col = (idx - row * n4) * 4;
+              const __nv_bfloat162 l01 = __floats2bfloat162_rn(v[u].x, v[u].y);
+              const __nv_bfloat162 l23 = __floats2bfloat162_rn(v[u].z, v[u].w);
               uint2 pk;
               pk.x = *reinterpret_cast<const uint32_t*>(&l01);
               pk.y = *reinterpret_cast<const uint32_t*>(&l23);
@@ -424,7 +439,7 @@ __global__ void __launch_bounds__(kThreads, 1) mttkrp_tc_kernel(const TcArgs a) 
           }
         }
       }
-      asm volatile("bar.sync 1, %0;" ::"r"(32 * kProducerWarps) : "memory");   // producer warps only
+      asm volatile("bar.sync 1, %0;" ::"r"(kStagers) : "memory");   // producer warps only
     }
     // this thread's column j of the unfolding: j = ia + Ia_pad * o, o mixed-radix
     // over the remaining modes; advanced incrementally by BK per k-step
@@ -700,8 +715,12 @@ __global__ void __launch_bounds__(kThreads, 1) mttkrp_tc_kernel(const TcArgs a) 
               float lo = __fadd_rn(e1, e2);
               const float hi = __fadd_rn(t, lo);
               lo = __fsub_rn(lo, __fsub_rn(hi, t));
-              const int k = Ec + __ldg(a.rowexp + i) - 2 * kSliceBits;
-              val = make_float2(ldexpf(hi, k), ldexpf(lo, k));
+              int k = Ec + __ldg(a.rowexp + i) - 2 * kSliceBits;
+              // 2^k as two exact power-of-two factors; beyond +-250 every FP32
+              // result has over- or underflowed already
+              k = k < -250 ? -250 : (k > 250 ? 250 : k);
+              const float s1 = pow2f(k >> 1), s2 = pow2f(k - (k >> 1));
+              val = make_float2(hi * s1 * s2, lo * s1 * s2);
             }
             out2[i * a.C + c] = val;
           }
