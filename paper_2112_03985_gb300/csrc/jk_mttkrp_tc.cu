@@ -40,9 +40,11 @@
 // instead of 10 for BN = 64.
 //
 // Exact-chain form (JKCALS_EXACT_BF16): every operand value x of a row whose
-// magnitudes stay below 2^E is written as x = 2^(E-7) (s0 + s1/2^7 + s2/2^14 +
-// s3/2^21) with integers |s_0| <= 128, |s_k| <= 64 (round-to-nearest
-// extraction, exact in FP32) and stored as BF16 s_k * 2^(-7k).  Products of
+// magnitudes stay below 2^E is written as x = 2^(E-7) (s0 + s1/2^7 + r2 + r3)
+// with integers |s_0| <= 128, |s_1| <= 64 (round-to-nearest extraction, exact
+// in FP32), stored as BF16 s_0 and s_1 * 2^-7, and two further BF16 slices r2,
+// r3 of the remainder (|r2| <= 2^-8; the T side keeps them on the grids 2^-14
+// and 2^-21, the Khatri-Rao side rounds them to 8 significant bits).  Products of
 // level 0 (s0 t0) and of level 1 (s0 t1 + s1 t0) are integer multiples of 1 and
 // 2^-7 whose chain sums stay below 2^24 units for chains of <= 1024 columns, so
 // they accumulate exactly in FP32 TMEM; levels 2 and 3 carry truncation scaled
@@ -184,38 +186,45 @@ __device__ __forceinline__ void split_value(float v, float (&p)[4]) {
 }
 
 // Exact-chain form, two Khatri-Rao entries at once: the pairs (u_e + ul_e) *
-// (qh + ql) as unevaluated FP32 pairs (error-free FMA products), scaled by the
-// row's power of two into [-128, 128] and cut into four slices on the grids
-// 2^(-7k): (r + M_k) - M_k with M_k = 1.5 * 2^(23 - 7k) rounds r to the nearest
-// multiple of 2^(-7k).  Every step is exact except adding the low part after
-// the first slice (error below 2^-25 of the grid unit).  Returns the BF16
-// patterns of the two entries' slices, one 32-bit word per slice.
-__device__ __forceinline__ void exact_slices2(f2 u, f2 ul, f2 qh2, f2 nqh2, f2 ql2, f2 sc2, uint32_t (&w)[4]) {
+// (qh + ql), with the row's power of two already folded into (qh, ql) so that
+// the product lies in [-128, 128], as unevaluated FP32 pairs (error-free FMA
+// products), cut into four BF16 slices.  Slices 0 and 1 feed the exactly
+// accumulated levels 0 and 1, so they are rounded onto the grids 1 and 2^-7:
+// (r + M_k) - M_k with M_k = 1.5 * 2^(23 - 7k) rounds r to the nearest
+// multiple of 2^(-7k).  Slices 2 and 3 only meet the truncating accumulators of
+// levels 2 and 3, so plain round-to-nearest BF16 conversion suffices (8
+// significant bits each; the remainder is below 2^-26).  Every step is exact
+// except adding the low part after the first slice.  Returns the BF16 patterns
+// of the two entries' slices, one 32-bit word per slice.
+__device__ __forceinline__ uint32_t cvt_bf16x2(f2 v) {   // {bf16(lo) | bf16(hi) << 16}
+  float lo, hi;
+  f2_unpack(v, lo, hi);
+  uint32_t d;
+  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
+  return d;
+}
+__device__ __forceinline__ f2 bf16x2_to_f2(uint32_t w) {
+  return f2_pack(__uint_as_float(w << 16), __uint_as_float(w & 0xffff0000u));
+}
+__device__ __forceinline__ void exact_slices2(f2 u, f2 ul, f2 qh2, f2 nqh2, f2 ql2, uint32_t (&w)[4]) {
   const f2 p = f2_mul(u, qh2);
   const f2 e1n = f2_fma(u, nqh2, p);                           // p - u qh, exact
   const f2 e2 = f2_fma(u, ql2, f2_mul(ul, qh2));               // u ql + ul qh
   const f2 vl = f2_sub(e2, e1n);
   const f2 m0 = f2_pack(12582912.f, 12582912.f);               // 1.5 * 2^23
   const f2 m1 = f2_pack(98304.f, 98304.f);                     // 1.5 * 2^16
-  const f2 m2 = f2_pack(768.f, 768.f);                         // 1.5 * 2^9
-  const f2 m3 = f2_pack(6.f, 6.f);                             // 1.5 * 2^2
-  f2 y = f2_mul(p, sc2);
-  const f2 s0 = f2_sub(f2_add(y, m0), m0);
-  y = f2_fma(vl, sc2, f2_sub(y, s0));
-  const f2 s1 = f2_sub(f2_add(y, m1), m1);
-  y = f2_sub(y, s1);
-  const f2 s2 = f2_sub(f2_add(y, m2), m2);
-  y = f2_sub(y, s2);
-  const f2 s3 = f2_sub(f2_add(y, m3), m3);
+  const f2 s0 = f2_sub(f2_add(p, m0), m0);
+  const f2 y1 = f2_add(f2_sub(p, s0), vl);
+  const f2 s1 = f2_sub(f2_add(y1, m1), m1);
+  const f2 y2 = f2_sub(y1, s1);
+  w[2] = cvt_bf16x2(y2);
+  const f2 y3 = f2_sub(y2, bf16x2_to_f2(w[2]));
+  w[3] = cvt_bf16x2(y3);
   float a, b;
   f2_unpack(s0, a, b);
   w[0] = pack_bf16_exact(a, b);
   f2_unpack(s1, a, b);
   w[1] = pack_bf16_exact(a, b);
-  f2_unpack(s2, a, b);
-  w[2] = pack_bf16_exact(a, b);
-  f2_unpack(s3, a, b);
-  w[3] = pack_bf16_exact(a, b);
 }
 
 // Error-free product of the pairs (qh + ql)(bh + bl), renormalised.
@@ -573,15 +582,14 @@ __global__ void __launch_bounds__(kThreads, 1) mttkrp_tc_kernel(const TcArgs a) 
             ul[0] = l0.x; ul[1] = l0.y; ul[2] = l0.z; ul[3] = l0.w;
             ul[4] = l1.x; ul[5] = l1.y; ul[6] = l1.z; ul[7] = l1.w;
           }
-          const float qh = live ? qhc[rr] : 0.f, ql = live ? qlc[rr] : 0.f;
+          // the row's power of two folded into Q (exact)
+          const float qh = live ? qhc[rr] * rscale[rr] : 0.f, ql = live ? qlc[rr] * rscale[rr] : 0.f;
           const f2 qh2 = f2_pack(qh, qh), nqh2 = f2_pack(-qh, -qh), ql2 = f2_pack(ql, ql);
-          const f2 sc2 = f2_pack(rscale[rr], rscale[rr]);
           uint32_t w[4][4];   // [slice][pair]
 #pragma unroll
           for (int e = 0; e < 4; ++e) {
             uint32_t ws[4];
-            exact_slices2(f2_pack(uh[2 * e], uh[2 * e + 1]), f2_pack(ul[2 * e], ul[2 * e + 1]), qh2, nqh2, ql2, sc2,
-                          ws);
+            exact_slices2(f2_pack(uh[2 * e], uh[2 * e + 1]), f2_pack(ul[2 * e], ul[2 * e + 1]), qh2, nqh2, ql2, ws);
 #pragma unroll
             for (int p = 0; p < 4; ++p) w[p][e] = ws[p];
           }
