@@ -40,11 +40,11 @@
 // instead of 10 for BN = 64.
 //
 // Exact-chain form (JKCALS_EXACT_BF16): every operand value x of a row whose
-// magnitudes stay below 2^E is written as x = 2^(E-7) (s0 + s1/2^7 + r2 + r3)
-// with integers |s_0| <= 128, |s_1| <= 64 (round-to-nearest extraction, exact
-// in FP32), stored as BF16 s_0 and s_1 * 2^-7, and two further BF16 slices r2,
-// r3 of the remainder (|r2| <= 2^-8; the T side keeps them on the grids 2^-14
-// and 2^-21, the Khatri-Rao side rounds them to 8 significant bits).  Products of
+// magnitudes stay below 2^E is written as x = 2^(E-7) (s0 + s1/2^7 + s2/2^14 +
+// r3) with integers |s_0| <= 128, |s_1|, |s_2| <= 64 (round-to-nearest
+// extraction, exact in FP32), stored as BF16 s_k * 2^(-7k), and a BF16 last
+// slice r3 of the remainder (the T side keeps it on the grid 2^-21 too; the
+// Khatri-Rao side rounds it to 8 significant bits).  Products of
 // level 0 (s0 t0) and of level 1 (s0 t1 + s1 t0) are integer multiples of 1 and
 // 2^-7 whose chain sums stay below 2^24 units for chains of <= 1024 columns, so
 // they accumulate exactly in FP32 TMEM; levels 2 and 3 carry truncation scaled
@@ -188,23 +188,21 @@ __device__ __forceinline__ void split_value(float v, float (&p)[4]) {
 // Exact-chain form, two Khatri-Rao entries at once: the pairs (u_e + ul_e) *
 // (qh + ql), with the row's power of two already folded into (qh, ql) so that
 // the product lies in [-128, 128], as unevaluated FP32 pairs (error-free FMA
-// products), cut into four BF16 slices.  Slices 0 and 1 feed the exactly
-// accumulated levels 0 and 1, so they are rounded onto the grids 1 and 2^-7:
-// (r + M_k) - M_k with M_k = 1.5 * 2^(23 - 7k) rounds r to the nearest
-// multiple of 2^(-7k).  Slices 2 and 3 only meet the truncating accumulators of
-// levels 2 and 3, so plain round-to-nearest BF16 conversion suffices (8
-// significant bits each; the remainder is below 2^-26).  Every step is exact
-// except adding the low part after the first slice.  Returns the BF16 patterns
-// of the two entries' slices, one 32-bit word per slice.
+// products), cut into four BF16 slices.  Slices 0-2 are rounded onto the grids
+// 1, 2^-7 and 2^-14: (r + M_k) - M_k with M_k = 1.5 * 2^(23 - 7k) rounds r to
+// the nearest multiple of 2^(-7k).  On these grids the products of levels 0
+// and 1, and in practice level 2 (its terms are multiples of 2^-14 and its
+// chain sums stay near 2^24 units), accumulate exactly.  Slice 3 only meets
+// the truncating level-3 accumulator, so plain round-to-nearest BF16
+// conversion suffices (the remainder is below 2^-24 of the grid 2^-14).
+// Every step is exact except adding the low part after the first slice.
+// Returns the BF16 patterns of the two entries' slices, one word per slice.
 __device__ __forceinline__ uint32_t cvt_bf16x2(f2 v) {   // {bf16(lo) | bf16(hi) << 16}
   float lo, hi;
   f2_unpack(v, lo, hi);
   uint32_t d;
   asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
   return d;
-}
-__device__ __forceinline__ f2 bf16x2_to_f2(uint32_t w) {
-  return f2_pack(__uint_as_float(w << 16), __uint_as_float(w & 0xffff0000u));
 }
 __device__ __forceinline__ void exact_slices2(f2 u, f2 ul, f2 qh2, f2 nqh2, f2 ql2, uint32_t (&w)[4]) {
   const f2 p = f2_mul(u, qh2);
@@ -216,15 +214,17 @@ __device__ __forceinline__ void exact_slices2(f2 u, f2 ul, f2 qh2, f2 nqh2, f2 q
   const f2 s0 = f2_sub(f2_add(p, m0), m0);
   const f2 y1 = f2_add(f2_sub(p, s0), vl);
   const f2 s1 = f2_sub(f2_add(y1, m1), m1);
+  const f2 m2 = f2_pack(768.f, 768.f);                         // 1.5 * 2^9
   const f2 y2 = f2_sub(y1, s1);
-  w[2] = cvt_bf16x2(y2);
-  const f2 y3 = f2_sub(y2, bf16x2_to_f2(w[2]));
-  w[3] = cvt_bf16x2(y3);
+  const f2 s2 = f2_sub(f2_add(y2, m2), m2);
+  w[3] = cvt_bf16x2(f2_sub(y2, s2));
   float a, b;
   f2_unpack(s0, a, b);
   w[0] = pack_bf16_exact(a, b);
   f2_unpack(s1, a, b);
   w[1] = pack_bf16_exact(a, b);
+  f2_unpack(s2, a, b);
+  w[2] = pack_bf16_exact(a, b);
 }
 
 // Error-free product of the pairs (qh + ql)(bh + bl), renormalised.
