@@ -218,7 +218,6 @@ jkcals_status make_tc_plan(jkcals_ctx* h) {
     if (h->opt.splits <= 0) S = std::min<int64_t>(S, std::max<int64_t>(1, ksteps / 4));
     S = std::max<int64_t>(1, std::min<int64_t>(S, ksteps));
     int64_t kchunk = ((ksteps + S - 1) / S) * bk;
-    if (exact) kchunk = std::min<int64_t>(kchunk, tc::kExactChainMax);   // exact chains
     p.kchunk = kchunk;
     p.splits = (int)((p.Jp + p.kchunk - 1) / p.kchunk);
     p.nkt = ksteps;
@@ -436,14 +435,13 @@ jkcals_status check_device_error(jkcals_ctx* h) {
 }
 
 // Set the split-K factor of mode n's MTTKRP to about S (clamped to the
-// column count; the exact-chain form keeps chains <= kExactChainMax columns).
+// column count).
 void set_mode_splits(jkcals_ctx* h, int n, int64_t S) {
   if (h->tc) {
     tc::TcPlan& p = h->tcplan[n];
     const int64_t bk = tc::form_bk(h->opt.precision);
     S = std::max<int64_t>(1, std::min<int64_t>(S, p.nkt));
     int64_t kchunk = ((p.nkt + S - 1) / S) * bk;
-    if (h->opt.precision == JKCALS_EXACT_BF16) kchunk = std::min<int64_t>(kchunk, tc::kExactChainMax);
     p.kchunk = kchunk;
     p.splits = (int)((p.Jp + kchunk - 1) / kchunk);
   } else {

@@ -80,6 +80,7 @@ constexpr int kThreads = 32 * kWarps;
 constexpr int kProducerWarps = 8;
 constexpr int kRowsPerWarp = 128 / kProducerWarps;   // rows of the A tile per producer warp
 constexpr int kEpilogueWarp0 = 4;
+constexpr int kEpilogueWarps = kWarps - kEpilogueWarp0;
 __device__ __forceinline__ bool is_producer_warp(int w) { return w >= 2 && (w & 3) != 1; }
 __device__ __forceinline__ int producer_index(int w) { return w - 2 - (w > 5) - (w > 9); }
 constexpr int kRowsM = 128;                          // MMA M
@@ -265,8 +266,10 @@ __global__ void __launch_bounds__(kThreads, 1) mttkrp_tc_kernel(const TcArgs a) 
   uint64_t* bars = reinterpret_cast<uint64_t*>(ua_lo + ua_ln);
   uint64_t* full = bars;          // stage written: producer warps + the TMA arrival and its bytes
   uint64_t* empty = bars + S;     // stage consumed: the MMAs' commit
-  uint64_t* accum = bars + 2 * S;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accum + 1);
+  uint64_t* accum = bars + 2 * S;        // a segment's MMAs are complete
+  uint64_t* tmem_empty = accum + 1;       // the epilogue warps drained a segment
+  uint64_t* drain = accum + 2;            // abort path: the MMAs issued so far are complete
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accum + 3);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
   const int c0 = blockIdx.x * kRowsM;
@@ -275,6 +278,12 @@ __global__ void __launch_bounds__(kThreads, 1) mttkrp_tc_kernel(const TcArgs a) 
   int64_t je = jb + a.kchunk;
   if (je > a.Jp) je = a.Jp;
   const int nk = (je > jb) ? (int)((je - jb + BK - 1) / BK) : 0;
+  // Exact-chain form: the exactly accumulated levels hold at most
+  // kExactChainMax columns, so a CTA's chain runs in segments of that length;
+  // after each the epilogue warps drain TMEM into the CTA's partial.  Other
+  // forms: one segment.
+  const int seg = Cfg::exact ? kExactChainMax / BK : (nk > 0 ? nk : 1);
+  const int nseg = (nk + seg - 1) / seg;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < S; ++s) {
@@ -282,6 +291,8 @@ __global__ void __launch_bounds__(kThreads, 1) mttkrp_tc_kernel(const TcArgs a) 
       mbar_init(&empty[s], 1);
     }
     mbar_init(accum, 1);
+    mbar_init(tmem_empty, kEpilogueWarps);
+    mbar_init(drain, 1);
     *abort_flag = 0;
     fence_barrier_init();
   }
@@ -328,6 +339,12 @@ __global__ void __launch_bounds__(kThreads, 1) mttkrp_tc_kernel(const TcArgs a) 
       bool ok = true;
       for (int it = 0; it < nk && ok; ++it) {
         const int s = it % S;
+        const int j = it / seg, kin = it - j * seg;
+        if (kin == 0 && j > 0) {
+          // the next segment overwrites the accumulators once they are drained
+          ok = wait_bounded(tmem_empty, (uint32_t)(j - 1) & 1u, abort_flag, a.err, 7);
+          if (!ok) break;
+        }
         ok = wait_bounded(&full[s], (uint32_t)(it / S) & 1u, abort_flag, a.err, 2);
         if (!ok) break;
         tc_fence_after();
@@ -338,21 +355,121 @@ __global__ void __launch_bounds__(kThreads, 1) mttkrp_tc_kernel(const TcArgs a) 
 #pragma unroll
           for (int m = 0; m < kMaxMma; ++m) {   // static indices: the list stays in the parameter bank
             if (m < nm) {
-              const bool first = it == 0 && kk == 0 && ((a.mma.first >> m) & 1u);
+              const bool first = kin == 0 && kk == 0 && ((a.mma.first >> m) & 1u);
               tc_mma<Cfg::kind>(tmem + a.mma.d[m], ad0 + (uint64_t)(a.mma.a[m] + 2 * kk),
                                 bd0 + (uint64_t)(a.mma.b[m] + 2 * kk), a.mma.idesc[m], first ? 0u : 1u);
             }
           }
         }
         tc_commit(&empty[s]);
+        if (kin == seg - 1 || it == nk - 1) tc_commit(accum);   // segment j complete
       }
-      // Always signal the accumulator: its phase completes once every MMA issued
-      // above has finished, so on an abort this lane drains them before TMEM is freed.
-      tc_commit(accum);
-      if (!ok) wait_drain(accum, 0);
+      // On an abort, wait (bounded) until every MMA issued so far has finished,
+      // so that TMEM is not freed under them.
+      if (!ok) {
+        tc_commit(drain);
+        wait_drain(drain, 0);
+      }
     }
   } else {
     bool ok = true;
+    int drained = 0;   // segments drained so far (epilogue warps)
+    // ---------------- epilogue: TMEM -> partial of Mbar_n, once per segment -------------
+    // Segment j's accumulators are added into this split's partial (stored for
+    // j = 0) and the MMA warp is released to overwrite them.  Warps 5 and 9
+    // share the MMA warp's scheduler: they sleep in the wait.
+    const int quarter = warp & 3;                      // TMEM lanes 32*quarter .. +31
+    const int grp = (warp - kEpilogueWarp0) >> 2;      // two warps per lane quarter split the columns
+    const int m_e = quarter * 32 + lane;
+    const int c_e = c0 + m_e;
+    int Ec = 0;
+    if constexpr (Cfg::exact) {
+      if (warp >= kEpilogueWarp0 && c_e < a.C)
+        Ec = bound_exponent_prod(__ldg(a.cmax_a + c_e), a.cmax_q, a.nq, c_e);
+    }
+    auto drain_segment = [&](int j) {
+      const int c = c_e;
+      bool have = ok && nk > 0 && wait_sleepy(accum, (uint32_t)j & 1u, abort_flag, a.err, 5);
+      have = __all_sync(0xffffffffu, have);   // tcgen05.ld is warp-collective
+      tc_fence_after();
+      const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16);
+      const uint32_t L = (uint32_t)a.lstride;
+      // 16-column slices (BN is a multiple of 16), dealt round-robin to the two
+      // warps of each lane quarter
+      for (int cc = 16 * grp; cc < a.BN && have; cc += 32) {
+        const uint32_t col = lane_base + (uint32_t)cc;
+        if constexpr (!Cfg::exact) {
+          uint32_t v0[32], v1[32], v2[32];
+          tmem_ld16(col, v0);
+          if (a.nlev > 1) tmem_ld16(col + L, v1);
+          if (a.nlev > 2) tmem_ld16(col + 2 * L, v2);
+          tmem_ld_wait();
+          float* out = a.part + (int64_t)blockIdx.z * a.I * a.C;
+#pragma unroll
+          for (int r = 0; r < 16; ++r) {
+            const int64_t i = (int64_t)n0 + cc + r;
+            if (i < a.I && c < a.C) {
+              float lo = 0.f;   // the smaller levels first
+              if (a.nlev > 2) lo = __uint_as_float(v2[r]);
+              if (a.nlev > 1) lo += __uint_as_float(v1[r]);
+              out[i * a.C + c] = __uint_as_float(v0[r]) + lo;
+            }
+          }
+        } else {
+          uint32_t v0[32], v1[32], v2[32], v3[32];
+          tmem_ld16(col, v0);
+          tmem_ld16(col + L, v1);
+          tmem_ld16(col + 2 * L, v2);
+          if (!a.merged) tmem_ld16(col + 3 * L, v3);
+          tmem_ld_wait();
+          // levels 0 and 1 are exact; add the levels as an unevaluated FP32 pair
+          // (hi, lo) with error-free TwoSum steps, scale by 2^(E_c + F_i - 14)
+          // and add the pair into the partial; the consumer adds hi + lo
+          float2* out2 = reinterpret_cast<float2*>(a.part) + (int64_t)blockIdx.z * a.I * a.C;
+#pragma unroll
+          for (int r = 0; r < 16; ++r) {
+            const int64_t i = (int64_t)n0 + cc + r;
+            if (i < a.I && c < a.C) {
+              const float l0 = __uint_as_float(v0[r]), l1 = __uint_as_float(v1[r]);
+              const float l2 = a.merged ? __uint_as_float(v2[r]) : __uint_as_float(v2[r]) + __uint_as_float(v3[r]);
+              const float s = __fadd_rn(l0, l1);
+              const float bb = __fsub_rn(s, l0);
+              const float e1 = __fadd_rn(__fsub_rn(l0, __fsub_rn(s, bb)), __fsub_rn(l1, bb));
+              const float t = __fadd_rn(s, l2);
+              const float b2 = __fsub_rn(t, s);
+              const float e2 = __fadd_rn(__fsub_rn(s, __fsub_rn(t, b2)), __fsub_rn(l2, b2));
+              float lo = __fadd_rn(e1, e2);
+              float hi = __fadd_rn(t, lo);
+              lo = __fsub_rn(lo, __fsub_rn(hi, t));
+              int k = Ec + __ldg(a.rowexp + i) - 2 * kSliceBits;
+              // 2^k as two exact power-of-two factors; beyond +-250 every FP32
+              // result has over- or underflowed already
+              k = k < -250 ? -250 : (k > 250 ? 250 : k);
+              const float s1 = pow2f(k >> 1), s2 = pow2f(k - (k >> 1));
+              hi = hi * s1 * s2;
+              lo = lo * s1 * s2;
+              if (j > 0) {
+                // double-float sum with the earlier segments' pair
+                const float2 o = out2[i * a.C + c];
+                const float sh = __fadd_rn(o.x, hi);
+                const float bv = __fsub_rn(sh, o.x);
+                const float eh = __fadd_rn(__fsub_rn(o.x, __fsub_rn(sh, bv)), __fsub_rn(hi, bv));
+                const float el = __fadd_rn(eh, __fadd_rn(o.y, lo));
+                hi = __fadd_rn(sh, el);
+                lo = __fsub_rn(el, __fsub_rn(hi, sh));
+              }
+              out2[i * a.C + c] = make_float2(hi, lo);
+            }
+          }
+        }
+      }
+      // this warp's TMEM reads are complete: release the accumulators
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(tmem_empty);
+      drained = j + 1;
+    };
+
     if (is_producer_warp(warp)) {
     // ---------------- Khatri-Rao producers ------------------------------------------
     const int pw = producer_index(warp);    // 0..kProducerWarps-1
@@ -523,7 +640,19 @@ __global__ void __launch_bounds__(kThreads, 1) mttkrp_tc_kernel(const TcArgs a) 
     load_raw(iq);
     form_q(iq);
     const uint32_t ring_s = smem_u32(ring);
-    for (int it = 0; it < nk && ok; ++it) {
+    // The k loop runs in stretches between this warp's drains (a drain of
+    // segment j comes after the warp has also filled the first stages of
+    // segment j + 1, so the MMA warp resumes without a gap); the drain code
+    // stays out of the hot loop.
+    const bool drains_here = warp >= kEpilogueWarp0;
+    int it = 0;
+    while (it < nk && ok) {
+      int stop = nk;
+      if (drains_here && drained < nseg - 1) {
+        const int end_j = (drained + 1) * seg - 1;
+        stop = end_j + S < nk ? end_j + S : nk;   // produce through end_j + S - 1
+      }
+    for (; it < stop && ok; ++it) {
       const int s = it % S;
       // next k-step's indices; on a carry fetch its factor entries now
       int ia_n = ia + BK;
@@ -647,95 +776,15 @@ __global__ void __launch_bounds__(kThreads, 1) mttkrp_tc_kernel(const TcArgs a) 
 #pragma unroll
       for (int t = 0; t < kMaxModes - 2; ++t) iq[t] = iq_n[t];
     }
+      if (drains_here && drained < nseg - 1 && it == stop && ok) drain_segment(drained);
+    }
 
     }   // producers
 
     if (warp >= kEpilogueWarp0) {
-    // ---------------- epilogue: TMEM -> partial of Mbar_n ----------------------------
-    // warps 5 and 9 share the MMA warp's scheduler: they sleep in the wait
-    bool have = ok && nk > 0 && wait_sleepy(accum, 0, abort_flag, a.err, 5);
-    have = __all_sync(0xffffffffu, have);   // tcgen05.ld is warp-collective
-    tc_fence_after();
-    const int quarter = warp & 3;                      // TMEM lanes 32*quarter .. +31
-    const int grp = (warp - kEpilogueWarp0) >> 2;      // two warps per lane quarter split the columns
-    const int m = quarter * 32 + lane;
-    const int c = c0 + m;
-    int Ec = 0;
-    if constexpr (Cfg::exact) {
-      if (c < a.C) Ec = bound_exponent_prod(__ldg(a.cmax_a + c), a.cmax_q, a.nq, c);
+      // segments not drained inside the producer loop
+      for (int j = drained; j < nseg; ++j) drain_segment(j);
     }
-    const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16);
-    const uint32_t L = (uint32_t)a.lstride;
-    // 16-column slices (BN is a multiple of 16), dealt round-robin to the two
-    // warps of each lane quarter
-    for (int cc = 16 * grp; cc < a.BN; cc += 32) {
-      const uint32_t col = lane_base + (uint32_t)cc;
-      if constexpr (!Cfg::exact) {
-        uint32_t v0[32], v1[32], v2[32];
-        if (have) {
-          tmem_ld16(col, v0);
-          if (a.nlev > 1) tmem_ld16(col + L, v1);
-          if (a.nlev > 2) tmem_ld16(col + 2 * L, v2);
-          tmem_ld_wait();
-        }
-        float* out = a.part + (int64_t)blockIdx.z * a.I * a.C;
-#pragma unroll
-        for (int r = 0; r < 16; ++r) {
-          const int64_t i = (int64_t)n0 + cc + r;
-          if (i < a.I && c < a.C) {
-            float x = 0.f;
-            if (have) {
-              float lo = 0.f;   // the smaller levels first
-              if (a.nlev > 2) lo = __uint_as_float(v2[r]);
-              if (a.nlev > 1) lo += __uint_as_float(v1[r]);
-              x = __uint_as_float(v0[r]) + lo;
-            }
-            out[i * a.C + c] = x;
-          }
-        }
-      } else {
-        uint32_t v0[32], v1[32], v2[32], v3[32];
-        if (have) {
-          tmem_ld16(col, v0);
-          tmem_ld16(col + L, v1);
-          tmem_ld16(col + 2 * L, v2);
-          if (!a.merged) tmem_ld16(col + 3 * L, v3);
-          tmem_ld_wait();
-        }
-        // levels 0 and 1 are exact; add the levels as an unevaluated FP32 pair
-        // (hi, lo) with error-free TwoSum steps, scale by 2^(E_c + F_i - 14) and
-        // store the pair; the consumer adds hi + lo
-        float2* out2 = reinterpret_cast<float2*>(a.part) + (int64_t)blockIdx.z * a.I * a.C;
-#pragma unroll
-        for (int r = 0; r < 16; ++r) {
-          const int64_t i = (int64_t)n0 + cc + r;
-          if (i < a.I && c < a.C) {
-            float2 val = make_float2(0.f, 0.f);
-            if (have) {
-              const float l0 = __uint_as_float(v0[r]), l1 = __uint_as_float(v1[r]);
-              const float l2 = a.merged ? __uint_as_float(v2[r]) : __uint_as_float(v2[r]) + __uint_as_float(v3[r]);
-              const float s = __fadd_rn(l0, l1);
-              const float bb = __fsub_rn(s, l0);
-              const float e1 = __fadd_rn(__fsub_rn(l0, __fsub_rn(s, bb)), __fsub_rn(l1, bb));
-              const float t = __fadd_rn(s, l2);
-              const float b2 = __fsub_rn(t, s);
-              const float e2 = __fadd_rn(__fsub_rn(s, __fsub_rn(t, b2)), __fsub_rn(l2, b2));
-              float lo = __fadd_rn(e1, e2);
-              const float hi = __fadd_rn(t, lo);
-              lo = __fsub_rn(lo, __fsub_rn(hi, t));
-              int k = Ec + __ldg(a.rowexp + i) - 2 * kSliceBits;
-              // 2^k as two exact power-of-two factors; beyond +-250 every FP32
-              // result has over- or underflowed already
-              k = k < -250 ? -250 : (k > 250 ? 250 : k);
-              const float s1 = pow2f(k >> 1), s2 = pow2f(k - (k >> 1));
-              val = make_float2(hi * s1 * s2, lo * s1 * s2);
-            }
-            out2[i * a.C + c] = val;
-          }
-        }
-      }
-    }
-    }   // epilogue
   }
 
   tc_fence_before();
@@ -865,7 +914,7 @@ size_t tc_smem_bytes(const TcPlan& p) {
   const size_t row = (size_t)p.row_bytes;
   const size_t a_stage = (size_t)p.nsplit * kRowsM * row;
   const size_t b_stage = (size_t)p.nsplit * p.BN * row;
-  return 1024 /*alignment slack*/ + (size_t)p.stages * (a_stage + b_stage) + tc_ua_bytes(p) + (2 * p.stages + 1) * 8 +
+  return 1024 /*alignment slack*/ + (size_t)p.stages * (a_stage + b_stage) + tc_ua_bytes(p) + (2 * p.stages + 3) * 8 +
          16;
 }
 

@@ -22,8 +22,9 @@ namespace jk {
 namespace tc {
 
 // Exact-chain sliced-BF16 form: 4 slices of 7-bit integers per operand on a
-// per-row power-of-two grid; a CTA's chain never exceeds this many columns of
-// T_(n), so that the two leading product levels sum exactly in FP32.
+// per-row power-of-two grid; the TMEM accumulators are drained after at most
+// this many columns of T_(n) (one segment of a CTA's chain), so that the two
+// leading product levels sum exactly in FP32.
 constexpr int kExactChainMax = 1024;
 constexpr int kSliceBits = 7;
 
