@@ -218,6 +218,22 @@ jkcals_status make_tc_plan(jkcals_ctx* h) {
     if (h->opt.splits <= 0) S = std::min<int64_t>(S, std::max<int64_t>(1, ksteps / 4));
     S = std::max<int64_t>(1, std::min<int64_t>(S, ksteps));
     int64_t kchunk = ((ksteps + S - 1) / S) * bk;
+    if (exact && h->opt.splits <= 0) {
+      // Exact chains stop every kExactChainMax columns.  Either each CTA runs
+      // one chain (many CTAs, several waves) or its chain in segments drained
+      // from TMEM in between (one wave, a drain per segment).  Estimated cost in
+      // k-steps per SM: waves x (k-steps + 3 per drain + 6 per CTA), the loop
+      // about 10% slower with segments.
+      const int64_t segk = tc::kExactChainMax / bk;
+      auto cost = [&](int64_t kc) {
+        const int64_t ks = kc / bk, nspl = (ksteps + ks - 1) / ks;
+        const int64_t waves = (base * nspl + h->num_sms - 1) / h->num_sms;
+        const int64_t nseg = (ks + segk - 1) / segk;
+        return (double)waves * (ks * (nseg > 1 ? 1.1 : 1.0) + 3.0 * (nseg - 1) + 6.0);
+      };
+      const int64_t capped = std::min<int64_t>(kchunk, tc::kExactChainMax);
+      if (cost(capped) <= cost(kchunk)) kchunk = capped;
+    }
     p.kchunk = kchunk;
     p.splits = (int)((p.Jp + p.kchunk - 1) / p.kchunk);
     p.nkt = ksteps;

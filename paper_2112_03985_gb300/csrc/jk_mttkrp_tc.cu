@@ -283,7 +283,7 @@ __global__ void __launch_bounds__(kThreads, 1) mttkrp_tc_kernel(const TcArgs a) 
   // after each the epilogue warps drain TMEM into the CTA's partial.  Other
   // forms: one segment.
   const int seg = Cfg::exact ? kExactChainMax / BK : (nk > 0 ? nk : 1);
-  const int nseg = (nk + seg - 1) / seg;
+  const int nseg = Cfg::exact ? (nk + seg - 1) / seg : (nk > 0 ? 1 : 0);
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < S; ++s) {
@@ -337,10 +337,10 @@ __global__ void __launch_bounds__(kThreads, 1) mttkrp_tc_kernel(const TcArgs a) 
       const uint64_t desc0 = smem_desc<ROW>(smem_u32(ring));
       const int nm = a.mma.n;
       bool ok = true;
+      int j = 0, kin = 0;   // segment and k-step within it, tracked without divisions
       for (int it = 0; it < nk && ok; ++it) {
         const int s = it % S;
-        const int j = it / seg, kin = it - j * seg;
-        if (kin == 0 && j > 0) {
+        if (Cfg::exact && kin == 0 && j > 0) {
           // the next segment overwrites the accumulators once they are drained
           ok = wait_bounded(tmem_empty, (uint32_t)(j - 1) & 1u, abort_flag, a.err, 7);
           if (!ok) break;
@@ -363,6 +363,10 @@ __global__ void __launch_bounds__(kThreads, 1) mttkrp_tc_kernel(const TcArgs a) 
         }
         tc_commit(&empty[s]);
         if (kin == seg - 1 || it == nk - 1) tc_commit(accum);   // segment j complete
+        if (++kin == seg) {
+          kin = 0;
+          ++j;
+        }
       }
       // On an abort, wait (bounded) until every MMA issued so far has finished,
       // so that TMEM is not freed under them.
@@ -648,7 +652,7 @@ __global__ void __launch_bounds__(kThreads, 1) mttkrp_tc_kernel(const TcArgs a) 
     int it = 0;
     while (it < nk && ok) {
       int stop = nk;
-      if (drains_here && drained < nseg - 1) {
+      if (Cfg::exact && drains_here && drained < nseg - 1) {
         const int end_j = (drained + 1) * seg - 1;
         stop = end_j + S < nk ? end_j + S : nk;   // produce through end_j + S - 1
       }
@@ -776,7 +780,7 @@ __global__ void __launch_bounds__(kThreads, 1) mttkrp_tc_kernel(const TcArgs a) 
 #pragma unroll
       for (int t = 0; t < kMaxModes - 2; ++t) iq[t] = iq_n[t];
     }
-      if (drains_here && drained < nseg - 1 && it == stop && ok) drain_segment(drained);
+      if (Cfg::exact && drains_here && drained < nseg - 1 && it == stop && ok) drain_segment(drained);
     }
 
     }   // producers
