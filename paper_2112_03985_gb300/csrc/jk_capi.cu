@@ -314,7 +314,7 @@ jkcals_status enqueue_mttkrp(jkcals_ctx* h, int n, double* const* U, float* cons
   a.nlev = p.nlev;
   a.lstride = p.lstride;
   a.merged = p.merged;
-  a.mma = p.mma;
+  a.stack = p.stack;
   a.nkt = p.nkt;
   a.Tt = static_cast<const unsigned char*>(h->Tt[n]);
   a.stages = p.stages;

@@ -78,6 +78,7 @@ struct TcPlan {
   int nlev;        // accumulators (product levels) in TMEM
   int lstride;     // TMEM columns between accumulators (multiple of 32)
   int merged;      // exact form with BN > 128: levels 2 and 3 share an accumulator
+  int stack;       // B parts stacked per MMA along N (1, 2 or 4; 1 when merged)
   int nsplit;      // operand parts of the form
   int row_bytes;   // bytes of K per operand row and stage (128 or 64)
   int a_mode;      // fastest other mode

@@ -236,6 +236,33 @@ __device__ __forceinline__ void pair_mul(float& qh, float& ql, float bh, float b
   ql = eq;
 }
 
+// The MMAs of one 32-byte K slice kk of a stage, unrolled at compile time for
+// P operand parts, B parts stacked G at a time along N and, for MERGED, levels
+// 2 and 3 sharing one accumulator: A part s times B parts t0..t1 into TMEM
+// columns (level of s + t0) * L.  (A list read from kernel parameters at run
+// time costs the issuing lane about half the stage time.)  Only BN enters at
+// run time: the B part stride b_bytes and the N field, idesc[c] for c parts.
+template <class Cfg, int G, bool MERGED>
+__device__ __forceinline__ void issue_slice(uint32_t tmem, uint64_t ad0, uint64_t bd0, uint32_t L, uint32_t b16,
+                                            const uint32_t (&idesc)[5], int kk, bool first_slice) {
+  constexpr int P = Cfg::nsplit;
+  constexpr uint32_t a16 = (uint32_t)(128 * Cfg::row_bytes) >> 4;   // A part stride in 16-byte units
+#pragma unroll
+  for (int s = 0; s < P; ++s) {
+#pragma unroll
+    for (int t0 = 0; t0 < P - s; t0 += G) {
+      const int cnt = (t0 + G <= P - s) ? G : P - s - t0;
+      const int lev = MERGED ? (s + t0 < 2 ? s + t0 : 2) : s + t0;
+      // an MMA overwrites its columns on the chain's first slice iff none of
+      // its levels was written before it: the s = 0 MMAs (merged: the first
+      // one per level)
+      const bool fresh = s == 0 && (!MERGED || t0 <= 2);
+      tc_mma<Cfg::kind>(tmem + (uint32_t)lev * L, ad0 + (uint64_t)(s * a16 + 2 * kk),
+                        bd0 + (uint64_t)((uint32_t)t0 * b16 + 2 * kk), idesc[cnt], (first_slice && fresh) ? 0u : 1u);
+    }
+  }
+}
+
 template <class Cfg>
 __global__ void __launch_bounds__(kThreads, 1) mttkrp_tc_kernel(const TcArgs a) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -335,7 +362,13 @@ __global__ void __launch_bounds__(kThreads, 1) mttkrp_tc_kernel(const TcArgs a) 
       // bits, so every operand descriptor is the region's base descriptor plus
       // (byte offset >> 4): the list holds those offsets per MMA.
       const uint64_t desc0 = smem_desc<ROW>(smem_u32(ring));
-      const int nm = a.mma.n;
+      const uint32_t L = (uint32_t)a.lstride, b16 = b_bytes >> 4;
+      uint32_t idesc[5];   // FP32 accumulator, A/B formats, both K-major, N = c BN, M = 128
+#pragma unroll
+      for (int c = 0; c < 5; ++c)
+        idesc[c] = (1u << 4) | ((uint32_t)Cfg::fmt << 7) | ((uint32_t)Cfg::fmt << 10) |
+                   (((uint32_t)(c * a.BN) >> 3) << 17) | ((uint32_t)(kRowsM >> 4) << 24);
+      const int variant = a.merged ? 0 : (a.stack >= 4 ? 4 : a.stack);   // uniform over the kernel
       bool ok = true;
       int j = 0, kin = 0;   // segment and k-step within it, tracked without divisions
       for (int it = 0; it < nk && ok; ++it) {
@@ -352,13 +385,12 @@ __global__ void __launch_bounds__(kThreads, 1) mttkrp_tc_kernel(const TcArgs a) 
         const uint64_t bd0 = ad0 + (uint64_t)(a_stage >> 4);
 #pragma unroll
         for (int kk = 0; kk < ROW / 32; ++kk) {
-#pragma unroll
-          for (int m = 0; m < kMaxMma; ++m) {   // static indices: the list stays in the parameter bank
-            if (m < nm) {
-              const bool first = kin == 0 && kk == 0 && ((a.mma.first >> m) & 1u);
-              tc_mma<Cfg::kind>(tmem + a.mma.d[m], ad0 + (uint64_t)(a.mma.a[m] + 2 * kk),
-                                bd0 + (uint64_t)(a.mma.b[m] + 2 * kk), a.mma.idesc[m], first ? 0u : 1u);
-            }
+          const bool first = kin == 0 && kk == 0;
+          switch (variant) {
+            case 4: issue_slice<Cfg, 4, false>(tmem, ad0, bd0, L, b16, idesc, kk, first); break;
+            case 2: issue_slice<Cfg, 2, false>(tmem, ad0, bd0, L, b16, idesc, kk, first); break;
+            case 1: issue_slice<Cfg, 1, false>(tmem, ad0, bd0, L, b16, idesc, kk, first); break;
+            default: issue_slice<Cfg, 1, true>(tmem, ad0, bd0, L, b16, idesc, kk, first); break;
           }
         }
         tc_commit(&empty[s]);
@@ -804,22 +836,27 @@ __global__ void __launch_bounds__(kThreads, 1) mttkrp_tc_kernel(const TcArgs a) 
 // taken (TF32 / BF16: one; 3xTF32: hh, hl, lh; BF16x3: six; exact: ten).
 
 struct CfgTF32 {
+  static constexpr int fmt = 2;   // A/B format: TF32 2, BF16 1
   static constexpr int kind = kKindTF32, nsplit = 1, row_bytes = 128, elem = 4;
   static constexpr bool exact = false;
 };
 struct Cfg3xTF32 {
+  static constexpr int fmt = 2;   // A/B format: TF32 2, BF16 1
   static constexpr int kind = kKindTF32, nsplit = 2, row_bytes = 128, elem = 4;
   static constexpr bool exact = false;
 };
 struct CfgBF16 {
+  static constexpr int fmt = 1;   // A/B format: TF32 2, BF16 1
   static constexpr int kind = kKindBF16, nsplit = 1, row_bytes = 128, elem = 2;
   static constexpr bool exact = false;
 };
 struct CfgBF16x3 {
+  static constexpr int fmt = 1;   // A/B format: TF32 2, BF16 1
   static constexpr int kind = kKindBF16, nsplit = 3, row_bytes = 128, elem = 2;
   static constexpr bool exact = false;
 };
 struct CfgExact {
+  static constexpr int fmt = 1;   // A/B format: TF32 2, BF16 1
   static constexpr int kind = kKindBF16, nsplit = 4, row_bytes = 64, elem = 2;
   static constexpr bool exact = true;
 };
@@ -881,6 +918,7 @@ int build_mma_list(int precision, TcPlan& p) {
   while (p.tmem_cols < nacc * p.lstride) p.tmem_cols *= 2;
   // parts stack along N when each level starts right where the previous ends
   const int G = (!p.merged && p.lstride == p.BN) ? 256 / p.BN : 1;
+  p.stack = G >= 4 ? 4 : G;
   const uint32_t a_bytes = (uint32_t)kRowsM * p.row_bytes, b_bytes = (uint32_t)p.BN * p.row_bytes;
   auto level = [&](int l) { return l > nacc - 1 ? nacc - 1 : l; };
   MmaList& L = p.mma;

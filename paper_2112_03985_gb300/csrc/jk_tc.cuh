@@ -34,6 +34,7 @@ struct TcArgs {
   int C, BN, tmem_cols;
   int stages;                      // pipeline depth
   int nlev, lstride, merged;       // accumulators in TMEM (see TcPlan)
+  int stack;                       // B parts stacked per MMA along N
   int Ia_pad;
   int64_t nkt;                     // k-steps per N tile in Tt
   const unsigned char* Tt;         // pre-tiled unfolding (layout above)
@@ -52,7 +53,6 @@ struct TcArgs {
   const int* rowexp;               // I_n: F_i of this mode's unfolding
   int ua_smem;                     // stage the 128 rows of UTa (and UTa_lo) in shared memory
   int ua_stride;                   // floats per staged FP32 row (BF16 low rows: Ia_pad elements)
-  MmaList mma;                     // MMAs per 32-byte K slice
 };
 
 int form_nsplit(int precision);
