@@ -298,6 +298,7 @@ __global__ void __launch_bounds__(kThreads, 1) mttkrp_tc_kernel(const TcArgs a) 
   uint64_t* drain = accum + 2;            // abort path: the MMAs issued so far are complete
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accum + 3);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  int* srowexp = const_cast<int*>(abort_flag + 1);   // BN row exponents of this N tile (exact form)
 
   const int c0 = blockIdx.x * kRowsM;
   const int n0 = blockIdx.y * a.BN;
@@ -324,6 +325,13 @@ __global__ void __launch_bounds__(kThreads, 1) mttkrp_tc_kernel(const TcArgs a) 
     fence_barrier_init();
   }
   if (warp == 1) tmem_alloc(tmem_slot, (uint32_t)a.tmem_cols);
+  if constexpr (Cfg::exact) {
+    // the drains scale every row by its exponent: read them once
+    if ((int)threadIdx.x < a.BN) {
+      const int64_t i = (int64_t)n0 + threadIdx.x;
+      srowexp[threadIdx.x] = i < a.I ? __ldg(a.rowexp + i) : 0;
+    }
+  }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -477,7 +485,7 @@ __global__ void __launch_bounds__(kThreads, 1) mttkrp_tc_kernel(const TcArgs a) 
               float lo = __fadd_rn(e1, e2);
               float hi = __fadd_rn(t, lo);
               lo = __fsub_rn(lo, __fsub_rn(hi, t));
-              int k = Ec + __ldg(a.rowexp + i) - 2 * kSliceBits;
+              int k = Ec + srowexp[cc + r] - 2 * kSliceBits;
               // 2^k as two exact power-of-two factors; beyond +-250 every FP32
               // result has over- or underflowed already
               k = k < -250 ? -250 : (k > 250 ? 250 : k);
@@ -541,67 +549,6 @@ __global__ void __launch_bounds__(kThreads, 1) mttkrp_tc_kernel(const TcArgs a) 
       ua_row[rr] = smem_u32(ua_hi + (size_t)m * a.ua_stride);
       ua_rowl[rr] = smem_u32(ua_lo + (size_t)m * a.Ia_pad);
       rscale[rr] = 1.f;
-      if constexpr (Cfg::exact) {
-        if (cval[rr]) rscale[rr] = pow2f(7 - bound_exponent_prod(__ldg(a.cmax_a + c), a.cmax_q, a.nq, c));
-      }
-    }
-    if (a.ua_smem) {
-      // stage the CTA's 128 factor rows of mode a once (FP32 hi; BF16 lo for
-      // the exact form; zero past C): the k loop then reads them from shared
-      // memory instead of L2
-      constexpr int kStagers = 32 * kProducerWarps;
-      constexpr int kU = 4;   // loads in flight per thread
-      const int tid = pw * 32 + lane;
-      const int n4 = a.Ia_pad / 4;
-      for (int idx0 = tid; idx0 < kRowsM * n4; idx0 += kU * kStagers) {
-        float4 v[kU];
-#pragma unroll
-        for (int u = 0; u < kU; ++u) {
-          const int idx = idx0 + u * kStagers;
-          const int row = idx / n4, col = (idx - row * n4) * 4;
-          v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
-          if (idx < kRowsM * n4 && c0 + row < a.C)
-            v[u] = __ldg(reinterpret_cast<const float4*>(a.UTa + (int64_t)(c0 + row) * a.Ia_pad + col));
-        }
-#pragma unroll
-        for (int u = 0; u < kU; ++u) {
-          const int idx = idx0 + u * kStagers;
-          if (idx < kRowsM * n4) {
-            const int row = idx / n4, col = (idx - row * n4) * 4;
-            sts128(smem_u32(ua_hi + (size_t)row * a.ua_stride + col),
-                   make_uint4(__float_as_uint(v[u].x), __float_as_uint(v[u].y), __float_as_uint(v[u].z),
-                              __float_as_uint(v[u].w)));
-          }
-        }
-      }
-      if constexpr (Cfg::exact) {
-        // FP32 low parts rounded to BF16 (the pair then holds U to ~2^-32)
-        for (int idx0 = tid; idx0 < kRowsM * n4; idx0 += kU * kStagers) {
-          float4 v[kU];
-#pragma unroll
-          for (int u = 0; u < kU; ++u) {
-            const int idx = idx0 + u * kStagers;
-            const int row = idx / n4, col = (idx - row * n4) * 4;
-            v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (idx < kRowsM * n4 && c0 + row < a.C)
-              v[u] = __ldg(reinterpret_cast<const float4*>(a.UTa_lo + (int64_t)(c0 + row) * a.Ia_pad + col));
-          }
-#pragma unroll
-          for (int u = 0; u < kU; ++u) {
-            const int idx = idx0 + u * kStagers;
-            if (idx < kRowsM * n4) {
-              const int row = idx / n4, col = (idx - row * n4) * 4;
-              const __nv_bfloat162 l01 = __floats2bfloat162_rn(v[u].x, v[u].y);
-              const __nv_bfloat162 l23 = __floats2bfloat162_rn(v[u].z, v[u].w);
-              uint2 pk;
-              pk.x = *reinterpret_cast<const uint32_t*>(&l01);
-              pk.y = *reinterpret_cast<const uint32_t*>(&l23);
-              *reinterpret_cast<uint2*>(ua_lo + (size_t)row * a.Ia_pad + col) = pk;
-            }
-          }
-        }
-      }
-      asm volatile("bar.sync 1, %0;" ::"r"(kStagers) : "memory");   // producer warps only
     }
     // this thread's column j of the unfolding: j = ia + Ia_pad * o, o mixed-radix
     // over the remaining modes; advanced incrementally by BK per k-step
@@ -673,7 +620,72 @@ __global__ void __launch_bounds__(kThreads, 1) mttkrp_tc_kernel(const TcArgs a) 
         qlc[rr] = ql;
       }
     };
+    // prologue: the first remaining-mode entries are in flight while the factor
+    // rows are staged; the row scales are formed after it
     load_raw(iq);
+    if (a.ua_smem) {
+      // stage the CTA's 128 factor rows of mode a once (FP32 hi; BF16 lo for
+      // the exact form; zero past C): the k loop then reads them from shared
+      // memory instead of L2
+      constexpr int kStagers = 32 * kProducerWarps;
+      constexpr int kU = 4;   // loads in flight per thread
+      const int tid = pw * 32 + lane;
+      const int n4 = a.Ia_pad / 4;
+      for (int idx0 = tid; idx0 < kRowsM * n4; idx0 += kU * kStagers) {
+        float4 v[kU];
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+          const int idx = idx0 + u * kStagers;
+          const int row = idx / n4, col = (idx - row * n4) * 4;
+          v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (idx < kRowsM * n4 && c0 + row < a.C)
+            v[u] = __ldg(reinterpret_cast<const float4*>(a.UTa + (int64_t)(c0 + row) * a.Ia_pad + col));
+        }
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+          const int idx = idx0 + u * kStagers;
+          if (idx < kRowsM * n4) {
+            const int row = idx / n4, col = (idx - row * n4) * 4;
+            sts128(smem_u32(ua_hi + (size_t)row * a.ua_stride + col),
+                   make_uint4(__float_as_uint(v[u].x), __float_as_uint(v[u].y), __float_as_uint(v[u].z),
+                              __float_as_uint(v[u].w)));
+          }
+        }
+      }
+      if constexpr (Cfg::exact) {
+        // FP32 low parts rounded to BF16 (the pair then holds U to ~2^-32)
+        for (int idx0 = tid; idx0 < kRowsM * n4; idx0 += kU * kStagers) {
+          float4 v[kU];
+#pragma unroll
+          for (int u = 0; u < kU; ++u) {
+            const int idx = idx0 + u * kStagers;
+            const int row = idx / n4, col = (idx - row * n4) * 4;
+            v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (idx < kRowsM * n4 && c0 + row < a.C)
+              v[u] = __ldg(reinterpret_cast<const float4*>(a.UTa_lo + (int64_t)(c0 + row) * a.Ia_pad + col));
+          }
+#pragma unroll
+          for (int u = 0; u < kU; ++u) {
+            const int idx = idx0 + u * kStagers;
+            if (idx < kRowsM * n4) {
+              const int row = idx / n4, col = (idx - row * n4) * 4;
+              const __nv_bfloat162 l01 = __floats2bfloat162_rn(v[u].x, v[u].y);
+              const __nv_bfloat162 l23 = __floats2bfloat162_rn(v[u].z, v[u].w);
+              uint2 pk;
+              pk.x = *reinterpret_cast<const uint32_t*>(&l01);
+              pk.y = *reinterpret_cast<const uint32_t*>(&l23);
+              *reinterpret_cast<uint2*>(ua_lo + (size_t)row * a.Ia_pad + col) = pk;
+            }
+          }
+        }
+      }
+      asm volatile("bar.sync 1, %0;" ::"r"(kStagers) : "memory");   // producer warps only
+    }
+    if constexpr (Cfg::exact) {
+#pragma unroll
+      for (int rr = 0; rr < RPT; ++rr)
+        if (cval[rr]) rscale[rr] = pow2f(7 - bound_exponent_prod(__ldg(a.cmax_a + crow[rr]), a.cmax_q, a.nq, crow[rr]));
+    }
     form_q(iq);
     const uint32_t ring_s = smem_u32(ring);
     // The k loop runs in stretches between this warp's drains (a drain of
@@ -957,7 +969,7 @@ size_t tc_smem_bytes(const TcPlan& p) {
   const size_t a_stage = (size_t)p.nsplit * kRowsM * row;
   const size_t b_stage = (size_t)p.nsplit * p.BN * row;
   return 1024 /*alignment slack*/ + (size_t)p.stages * (a_stage + b_stage) + tc_ua_bytes(p) + (2 * p.stages + 3) * 8 +
-         16;
+         16 + 4 * (size_t)p.BN;
 }
 
 cudaError_t prepare_mttkrp_tc(int precision, size_t max_smem) {
