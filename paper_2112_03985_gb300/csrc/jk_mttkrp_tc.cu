@@ -12,9 +12,9 @@
 //   warp 0      TMA producer: streams BN-row tiles of the (pre-split) unfolding
 //               T_(n) into the B half of each pipeline stage.  The unfolding is
 //               stored pre-tiled in the exact shared-memory image of a stage
-//               (K-major, 128- or 64-byte swizzle), so each stage is one
-//               contiguous bulk copy per part instead of BN short rows strided
-//               across T_(n).
+//               (K-major, 128- or 64-byte swizzle, parts adjacent), so each stage
+//               is one contiguous bulk copy instead of BN short rows strided
+//               across T_(n); lane s issues the copies of ring stage s.
 //   warp 1      owns TMEM; one lane issues the stage's tcgen05.mma list
 //               (kind::tf32, or kind::f16 with BF16 operands), FP32 accumulators
 //               in TMEM.  It is alone on its scheduler (warps 5 and 9, which share
@@ -339,19 +339,21 @@ __global__ void __launch_bounds__(kThreads, 1) mttkrp_tc_kernel(const TcArgs a) 
 
   if (warp == 0) {
     // ---------------- TMA producer: tiles of T_(n) ------------------------------
-    if (lane == 0) {
+    // Lane s serves ring stage s: one bulk copy of the stage's B parts (contiguous
+    // in the pre-tiled image and in the ring) per k-step it = s, s + S, ...  One
+    // thread's bulk copies complete one after another (~0.3-0.4 us each for
+    // 4-40 KB from L2), copies from different threads overlap, so the loads of
+    // the S stages are issued by S lanes.
+    if (lane < S) {
       int issued = 0;
       // this CTA's first stage image: N tile blockIdx.y, k-step jb / BK
       const unsigned char* src = a.Tt + ((int64_t)blockIdx.y * a.nkt + jb / BK) * (int64_t)b_stage;
-      for (int it = 0; it < nk; ++it) {
-        const int s = it % S;
-        const uint32_t ph = (uint32_t)(it / S) & 1u;
-        if (!wait_bounded(&empty[s], ph ^ 1u, abort_flag, a.err, 1)) break;
-        mbar_arrive_expect_tx(&full[s], b_stage);
-        unsigned char* dst = ring + (size_t)s * stage_bytes + a_stage;
-#pragma unroll
-        for (int p = 0; p < NS; ++p) bulk_load(dst + p * b_bytes, src + p * b_bytes, b_bytes, &full[s]);
-        src += b_stage;
+      unsigned char* dst = ring + (size_t)lane * stage_bytes + a_stage;
+      uint32_t ph = 0;   // parity of this stage's pass
+      for (int it = lane; it < nk; it += S, ph ^= 1u) {
+        if (!wait_bounded(&empty[lane], ph ^ 1u, abort_flag, a.err, 1)) break;
+        mbar_arrive_expect_tx(&full[lane], b_stage);
+        bulk_load(dst, src + (int64_t)it * b_stage, b_stage, &full[lane]);
         issued = it + 1;
       }
       if (*abort_flag && issued > 0) {
@@ -379,14 +381,15 @@ __global__ void __launch_bounds__(kThreads, 1) mttkrp_tc_kernel(const TcArgs a) 
       const int variant = a.merged ? 0 : (a.stack >= 4 ? 4 : a.stack);   // uniform over the kernel
       bool ok = true;
       int j = 0, kin = 0;   // segment and k-step within it, tracked without divisions
+      int s = 0;            // ring stage and the parity of its pass, likewise
+      uint32_t ph = 0;
       for (int it = 0; it < nk && ok; ++it) {
-        const int s = it % S;
         if (Cfg::exact && kin == 0 && j > 0) {
           // the next segment overwrites the accumulators once they are drained
           ok = wait_bounded(tmem_empty, (uint32_t)(j - 1) & 1u, abort_flag, a.err, 7);
           if (!ok) break;
         }
-        ok = wait_bounded(&full[s], (uint32_t)(it / S) & 1u, abort_flag, a.err, 2);
+        ok = wait_bounded(&full[s], ph, abort_flag, a.err, 2);
         if (!ok) break;
         tc_fence_after();
         const uint64_t ad0 = desc0 + (uint64_t)(((uint32_t)s * stage_bytes) >> 4);
@@ -406,6 +409,10 @@ __global__ void __launch_bounds__(kThreads, 1) mttkrp_tc_kernel(const TcArgs a) 
         if (++kin == seg) {
           kin = 0;
           ++j;
+        }
+        if (++s == S) {
+          s = 0;
+          ph ^= 1u;
         }
       }
       // On an abort, wait (bounded) until every MMA issued so far has finished,
@@ -694,6 +701,8 @@ __global__ void __launch_bounds__(kThreads, 1) mttkrp_tc_kernel(const TcArgs a) 
     // stays out of the hot loop.
     const bool drains_here = warp >= kEpilogueWarp0;
     int it = 0;
+    int s = 0;          // ring stage of k-step it and the parity of its pass
+    uint32_t ph = 0;
     while (it < nk && ok) {
       int stop = nk;
       if (Cfg::exact && drains_here && drained < nseg - 1) {
@@ -701,7 +710,6 @@ __global__ void __launch_bounds__(kThreads, 1) mttkrp_tc_kernel(const TcArgs a) 
         stop = end_j + S < nk ? end_j + S : nk;   // produce through end_j + S - 1
       }
     for (; it < stop && ok; ++it) {
-      const int s = it % S;
       // next k-step's indices; on a carry fetch its factor entries now
       int ia_n = ia + BK;
       int iq_n[kMaxModes - 2];
@@ -722,7 +730,7 @@ __global__ void __launch_bounds__(kThreads, 1) mttkrp_tc_kernel(const TcArgs a) 
       if (wrap) load_raw(iq_n);
       // one lane per warp polls the barrier; __syncwarp orders the others after it
       bool got = true;
-      if (lane == 0) got = wait_bounded(&empty[s], ((uint32_t)(it / S) & 1u) ^ 1u, abort_flag, a.err, 4);
+      if (lane == 0) got = wait_bounded(&empty[s], ph ^ 1u, abort_flag, a.err, 4);
       got = __shfl_sync(0xffffffffu, got, 0);
       __syncwarp();
       if (!got) {
@@ -823,6 +831,10 @@ __global__ void __launch_bounds__(kThreads, 1) mttkrp_tc_kernel(const TcArgs a) 
       ia = ia_n;
 #pragma unroll
       for (int t = 0; t < kMaxModes - 2; ++t) iq[t] = iq_n[t];
+      if (++s == S) {
+        s = 0;
+        ph ^= 1u;
+      }
     }
       if (Cfg::exact && drains_here && drained < nseg - 1 && it == stop && ok) drain_segment(drained);
     }
