@@ -107,12 +107,26 @@ __global__ void __launch_bounds__(NT) mttkrp_f64_kernel(const double* __restrict
   }
 }
 
+// The split-K reductions below add the S partials of an element in split order.
+// A thread first loads a batch of kRedBatch partials (independent loads, all in
+// flight together), then adds them in order: one L2 round trip per batch
+// instead of one per split.
+constexpr int kRedBatch = 8;
+
 __global__ void reduce_partials_f64_kernel(const double* __restrict__ part, int S, int64_t count,
                                            double* __restrict__ out) {
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < count;
        e += (int64_t)gridDim.x * blockDim.x) {
-    double acc = part[e];
-    for (int s = 1; s < S; ++s) acc += part[(int64_t)s * count + e];
+    double acc = 0.0;
+    for (int s0 = 0; s0 < S; s0 += kRedBatch) {
+      double v[kRedBatch];
+#pragma unroll
+      for (int u = 0; u < kRedBatch; ++u) v[u] = s0 + u < S ? __ldg(part + (int64_t)(s0 + u) * count + e) : 0.0;
+#pragma unroll
+      for (int u = 0; u < kRedBatch; ++u) {
+        if (s0 + u < S) acc = (s0 + u == 0) ? v[u] : acc + v[u];
+      }
+    }
     out[e] = acc;
   }
 }
@@ -140,7 +154,14 @@ __global__ void reduce_partials_f32_kernel(const float* __restrict__ part, int S
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < count;
        e += (int64_t)gridDim.x * blockDim.x) {
     float hi = 0.f, lo = 0.f;
-    for (int s = 0; s < S; ++s) df_add(hi, lo, __ldg(part + (int64_t)s * count + e));
+    for (int s0 = 0; s0 < S; s0 += kRedBatch) {
+      float v[kRedBatch];
+#pragma unroll
+      for (int u = 0; u < kRedBatch; ++u) v[u] = s0 + u < S ? __ldg(part + (int64_t)(s0 + u) * count + e) : 0.f;
+#pragma unroll
+      for (int u = 0; u < kRedBatch; ++u)
+        if (s0 + u < S) df_add(hi, lo, v[u]);
+    }
     out[e] = df_to_double(hi, lo);
   }
 }
@@ -150,10 +171,18 @@ __global__ void reduce_partials_f32x2_kernel(const float2* __restrict__ part, in
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < count;
        e += (int64_t)gridDim.x * blockDim.x) {
     float hi = 0.f, lo = 0.f;
-    for (int s = 0; s < S; ++s) {
-      const float2 v = __ldg(part + (int64_t)s * count + e);
-      df_add(hi, lo, v.x);
-      lo = __fadd_rn(lo, v.y);
+    for (int s0 = 0; s0 < S; s0 += kRedBatch) {
+      float2 v[kRedBatch];
+#pragma unroll
+      for (int u = 0; u < kRedBatch; ++u)
+        v[u] = s0 + u < S ? __ldg(part + (int64_t)(s0 + u) * count + e) : make_float2(0.f, 0.f);
+#pragma unroll
+      for (int u = 0; u < kRedBatch; ++u) {
+        if (s0 + u < S) {
+          df_add(hi, lo, v[u].x);
+          lo = __fadd_rn(lo, v[u].y);
+        }
+      }
     }
     out[e] = df_to_double(hi, lo);
   }

@@ -31,6 +31,47 @@ __device__ __forceinline__ bool left_out(const BlockMeta& bm, int g, int64_t i) 
   return false;
 }
 
+// FP32 pair of a double u: hi = fl32(u), lo = fl32(u - hi), both rounded to
+// nearest even, as the conversions give them, but formed from u's bit pattern
+// with integer operations: the FP64 pipe (which also runs FP64 conversions) is
+// narrow on this part and the update is bound by it.  hi keeps the top 24
+// significant bits of u's 53 (round half to even on the low 29); u - hi is
+// that remainder, at most 29 bits, converted exactly to FP32 and scaled by the
+// power of two of its unit.  Magnitudes outside [2^-70, 2^120) (and 0, Inf,
+// NaN) take the conversions.
+__device__ __forceinline__ void split_f32_pair(double u, float& hi, float& lo) {
+  const long long bits = __double_as_longlong(u);
+  const uint32_t hw = (uint32_t)((unsigned long long)bits >> 32), lw = (uint32_t)bits;
+  const int e = (int)((hw >> 20) & 0x7ffu) - 1023;   // unbiased exponent
+  if (e < -70 || e >= 120) {
+    hi = __double2float_rn(u);
+    lo = __double2float_rn(u - (double)hi);
+    return;
+  }
+  const uint32_t sign = hw & 0x80000000u;
+  uint32_t keep = ((hw & 0xfffffu) << 3) | (lw >> 29);   // the 23 stored bits of hi
+  const uint32_t rem = lw & 0x1fffffffu;                  // the 29 bits below them
+  const bool up = rem > 0x10000000u || (rem == 0x10000000u && (keep & 1u));
+  uint32_t fexp = (uint32_t)(e + 127);
+  uint32_t r;   // |u - hi| in units of 2^(e - 52)
+  if (up) {
+    r = 0x20000000u - rem;
+    if (++keep == 0x800000u) {
+      keep = 0;
+      ++fexp;
+    }
+  } else {
+    r = rem;
+  }
+  hi = __uint_as_float(sign | (fexp << 23) | keep);
+  if (r == 0) {
+    lo = 0.f;
+    return;
+  }
+  const float mag = __uint2float_rn(r) * __uint_as_float((uint32_t)(e - 52 + 127) << 23);   // exact
+  lo = (up != (sign != 0u)) ? -mag : mag;   // u - hi has u's sign when hi was rounded down
+}
+
 // RMAX bounds the rank of every block; FIXED means every block has exactly RMAX
 // components, so the per-rank guards fold away at compile time.
 template <int RMAX, bool FIXED>
@@ -57,6 +98,7 @@ __global__ void __launch_bounds__(NT, FIXED ? 4 : 2) update_fused_kernel(UpdateA
   __shared__ double scale[RMAX];
   __shared__ double red[NT];
   __shared__ int spd_ok;
+  __shared__ int colmax[RMAX];   // FP32 bit patterns of max |hi| per column (non-negative: int order)
 
   for (int p = tid; p < R * R; p += NT) {
     double h = 1.0;
@@ -66,12 +108,29 @@ __global__ void __launch_bounds__(NT, FIXED ? 4 : 2) update_fused_kernel(UpdateA
     Hc[p] = h;
   }
   if (tid == 0) spd_ok = 1;
-  // this thread's first row of Mbar_n, loaded while warp 0 factorises H
-  double m[RMAX];
+  if (tid < RMAX) colmax[tid] = 0;
+  // this block's rows of Mbar_n into X, their loads in flight together with
+  // those of the Grams (a few rows per thread issued before any store)
   {
-    const int64_t i = tid;
+    constexpr int kLd = RMAX <= 8 ? 4 : 1;
+    for (int64_t i0 = tid; i0 < I; i0 += (int64_t)kLd * NT) {
+      double v[kLd][RMAX];
 #pragma unroll
-    for (int r = 0; r < RMAX; ++r) m[r] = (i < I && r < R) ? M[i * a.C + off + r] : 0.0;
+      for (int u = 0; u < kLd; ++u) {
+        const int64_t i = i0 + (int64_t)u * NT;
+#pragma unroll
+        for (int r = 0; r < RMAX; ++r) v[u][r] = (i < I && r < R) ? M[i * a.C + off + r] : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < kLd; ++u) {
+        const int64_t i = i0 + (int64_t)u * NT;
+        if (i < I) {
+#pragma unroll
+          for (int r = 0; r < RMAX; ++r)
+            if (r < R) X[i * R + r] = v[u][r];
+        }
+      }
+    }
   }
   __syncthreads();
   if (tid < 32) {
@@ -84,8 +143,12 @@ __global__ void __launch_bounds__(NT, FIXED ? 4 : 2) update_fused_kernel(UpdateA
           spd_ok = 0;
           d = 1.0;
         }
-        L[j][j] = sqrt(d);
-        invd[j] = 1.0 / L[j][j];
+        // 1 / L_jj straight from the reciprocal square root (the solves use
+        // only the reciprocals; one FP64 sequence instead of a root and a
+        // division on the serial path)
+        const double rs = rsqrt(d);
+        L[j][j] = d * rs;
+        invd[j] = rs;
       }
       __syncwarp();
       const int i = j + 1 + lane;
@@ -106,15 +169,12 @@ __global__ void __launch_bounds__(NT, FIXED ? 4 : 2) update_fused_kernel(UpdateA
     return;
   }
 
-  // solve every row; keep the rows in shared memory
+  // solve every row in place in X
   double fit = 0.0;
   for (int64_t i = tid; i < I; i += NT) {
-    double x[RMAX];
-    if (i != tid) {
-      const double* mrow = M + i * a.C + off;
+    double x[RMAX], m[RMAX];
 #pragma unroll
-      for (int r = 0; r < RMAX; ++r) m[r] = (r < R) ? mrow[r] : 0.0;
-    }
+    for (int r = 0; r < RMAX; ++r) m[r] = (r < R) ? X[i * R + r] : 0.0;
     if (a.n == a.n_hat && left_out(a.bm, g, i)) {
 #pragma unroll
       for (int r = 0; r < RMAX; ++r) x[r] = 0.0;
@@ -145,7 +205,7 @@ __global__ void __launch_bounds__(NT, FIXED ? 4 : 2) update_fused_kernel(UpdateA
     for (int r = 0; r < RMAX; ++r) {
       if (r < R) {
         X[i * R + r] = x[r];
-        fit = fma(x[r], m[r], fit);
+        if (last) fit = fma(x[r], m[r], fit);   // sum(x * m) enters the error only
       }
     }
   }
@@ -221,22 +281,20 @@ __global__ void __launch_bounds__(NT, FIXED ? 4 : 2) update_fused_kernel(UpdateA
     a.U[i * a.C + off + r] = X[t];
   }
   if (a.UT != nullptr) {
+    // transposed FP32 copies, and the column maxima of the high parts (the
+    // bound of |U| that the tensor-core form scales by)
     for (int64_t t = tid; t < I * R; t += NT) {
       const int r = (int)(t / I);
       const int64_t i = t - (int64_t)r * I;
-      const double u = X[i * R + r];
-      const float hi = (float)u;
+      float hi, lo;
+      split_f32_pair(X[i * R + r], hi, lo);
       a.UT[(int64_t)(off + r) * a.I_pad + i] = hi;
-      if (a.UT_lo != nullptr) a.UT_lo[(int64_t)(off + r) * a.I_pad + i] = (float)(u - (double)hi);
+      if (a.UT_lo != nullptr) a.UT_lo[(int64_t)(off + r) * a.I_pad + i] = lo;
+      if (a.cmax != nullptr) atomicMax(&colmax[r], __float_as_int(fabsf(hi)));
     }
     if (a.cmax != nullptr) {
-      const int warp = tid >> 5, lane = tid & 31;
-      for (int r = warp; r < R; r += NT / 32) {
-        float mx = 0.f;
-        for (int64_t i = lane; i < I; i += 32) mx = fmaxf(mx, fabsf((float)X[i * R + r]));
-        for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-        if (lane == 0) a.cmax[off + r] = mx;
-      }
+      __syncthreads();
+      if (tid < R) a.cmax[off + tid] = __int_as_float(colmax[tid]);
     }
   }
   for (int p = tid; p < R * R; p += NT) a.gram_n[go + p] = G[p / R][p % R];
@@ -263,9 +321,6 @@ __global__ void __launch_bounds__(NT, FIXED ? 4 : 2) update_fused_kernel(UpdateA
     a.loss_prev[g] = e;
   }
 }
-
-
-size_t update_fused_smem(int64_t I, int Rmax) { return (size_t)I * Rmax * sizeof(double); }
 
 // Instances: exact ranks 1..8 when all blocks share one rank, otherwise the
 // rank classes 8, 16, 32 with per-rank guards.
