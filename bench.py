@@ -38,7 +38,8 @@ L2_FLUSH_BYTES = 256 << 20
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=50)
+    p.add_argument("--steps", type=int, default=1000,
+                   help="timed sweeps (default: ~0.3 s of device time, long enough for the clock sampler)")
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--precision", default="exact_bf16")
@@ -106,7 +107,7 @@ class ClockSampler:
     def start(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                                          "-lms", "200", "-i", str(self.gpu_index)],
+                                          "-lms", "50", "-i", str(self.gpu_index)],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.proc = None
@@ -188,7 +189,9 @@ def reference_arm(args):
     import oracle as O
     from paper_2112_03985_gb300 import workloads as W
     w = W.make_config(2)
-    B = 24
+    # submodels per step: about 90 s of oracle work for the whole run (one
+    # submodel-sweep takes ~70 ms on 16 host cores), at least one
+    B = int(max(1, min(24, round(90.0 / (0.07 * max(1, args.steps))))))
     sel = list(range(0, w.K, w.K // B))[:B]
     state = []
     for g in sel:
@@ -358,15 +361,18 @@ def gpu_arm(args):
             "timing": "MTTKRP launches timed with CUDA events in a second pass of the same length "
                       "(event nodes around each launch); the headline pass has none"}
     losses_final = h.als_sweep(1)
-    U_ours = h.get_factors()
     h.close()
 
-    # plain FP64 on the same GPU (same workload, same sweep count) for the ratio and error
+    # plain FP64 on the same GPU (same workload, from the same start, the
+    # workload's sweep count) for the ratio and the factor error
     fp64 = None
     if args.precision != "fp64" and not args.no_fp64_compare:
+        with api.JKCALS(Td, w.n_hat, w.ranks, w.left_out, initd, precision=args.precision) as ha:
+            ha.als_sweep(w.sweeps)
+            U_ours = ha.get_factors()
         h64 = api.JKCALS(Td, w.n_hat, w.ranks, w.left_out, initd, precision="fp64")
-        n64 = max(3, min(args.steps, 10))
-        h64.als_sweep_async(args.warmup + args.steps - n64)
+        n64 = 10
+        h64.als_sweep_async(3)
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
@@ -378,7 +384,7 @@ def gpu_arm(args):
             e1.record(stream)
             torch.cuda.synchronize()
             tot += e0.elapsed_time(e1)
-        h64.als_sweep(1)
+        h64.als_sweep(w.sweeps - 3 - n64)
         U64 = h64.get_factors()
         h64.close()
         offs = np.concatenate([[0], np.cumsum(w.ranks)])
@@ -389,7 +395,7 @@ def gpu_arm(args):
                 err = max(err, float(np.linalg.norm(a - b) / np.linalg.norm(b)))
         fp64 = {"value": w.K * n64 / (tot / 1e3), "ratio": value / world / (w.K * n64 / (tot / 1e3)),
                 "factor_rel_err_vs_fp64_path": err,
-                "sweeps_compared": args.warmup + args.steps + 1}
+                "sweeps_compared": w.sweeps}
 
     # end to end: one whole job from pinned host buffers through the public API
     e2e = None
