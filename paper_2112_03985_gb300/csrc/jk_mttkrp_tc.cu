@@ -703,6 +703,7 @@ __global__ void __launch_bounds__(kThreads, 1) mttkrp_tc_kernel(const TcArgs a) 
     int it = 0;
     int s = 0;          // ring stage of k-step it and the parity of its pass
     uint32_t ph = 0;
+    bool pre = false;   // this stage seen released by a probe during the previous k-step
     while (it < nk && ok) {
       int stop = nk;
       if (Cfg::exact && drains_here && drained < nseg - 1) {
@@ -728,12 +729,19 @@ __global__ void __launch_bounds__(kThreads, 1) mttkrp_tc_kernel(const TcArgs a) 
         }
       }
       if (wrap) load_raw(iq_n);
-      // every lane polls the barrier (no divergent branch, no broadcast: ~2.5%
-      // faster than one polling lane); the vote keeps the warp's outcome uniform
-      const bool got = __all_sync(0xffffffffu, wait_bounded(&empty[s], ph ^ 1u, abort_flag, a.err, 4));
-      if (!got) {
-        ok = false;
-        break;
+      // The stage is nearly always released already: a probe issued during the
+      // previous k-step's work usually answers that, off the critical path;
+      // otherwise every lane polls the barrier (no divergent branch, no
+      // broadcast); the votes keep the warp's outcome uniform.
+      if (!__all_sync(0xffffffffu, pre)) {
+        if (!__all_sync(0xffffffffu, wait_bounded(&empty[s], ph ^ 1u, abort_flag, a.err, 4))) {
+          ok = false;
+          break;
+        }
+      }
+      {
+        const bool wrap_s = s + 1 == S;
+        pre = mbar_test_wait(&empty[wrap_s ? 0 : s + 1], (wrap_s ? ph ^ 1u : ph) ^ 1u);   // k-step it + 1
       }
       const bool jvalid = jcur < je32;
       const uint32_t a_tile_s = ring_s + (uint32_t)s * stage_bytes;
@@ -823,7 +831,7 @@ __global__ void __launch_bounds__(kThreads, 1) mttkrp_tc_kernel(const TcArgs a) 
       }
       fence_async_shared();   // each writer: generic-proxy stores -> visible to the MMA
       __syncwarp();
-      if (lane == 0) mbar_arrive(&full[s]);
+      mbar_arrive_lane0(&full[s], lane);
       if (wrap) form_q(iq_n);
       jcur += BK;
       ia = ia_n;
