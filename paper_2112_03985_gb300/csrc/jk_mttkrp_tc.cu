@@ -263,7 +263,10 @@ __device__ __forceinline__ void issue_slice(uint32_t tmem, uint64_t ad0, uint64_
   }
 }
 
-template <class Cfg>
+// QM: slots for the remaining modes beyond a that the producers track (the
+// column index carry, the factor entries of Q) — 2 covers tensors of up to 4
+// modes with short per-k-step index code, kMaxModes - 2 the rest.
+template <class Cfg, int QM>
 __global__ void __launch_bounds__(kThreads, 1) mttkrp_tc_kernel(const TcArgs a) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem =
@@ -562,13 +565,13 @@ __global__ void __launch_bounds__(kThreads, 1) mttkrp_tc_kernel(const TcArgs a) 
     const int je32 = (int)je;
     int jcur = (int)jb + q * CHUNK;
     int ia = 0;
-    int iq[kMaxModes - 2];
+    int iq[QM];
     {
       const int o = jcur / a.Ia_pad;
       ia = jcur - o * a.Ia_pad;
       int rem = o;
 #pragma unroll
-      for (int t = 0; t < kMaxModes - 2; ++t) {
+      for (int t = 0; t < QM; ++t) {
         iq[t] = 0;
         if (t < a.nq) {
           const int qq = rem / a.qdims[t];
@@ -583,7 +586,7 @@ __global__ void __launch_bounds__(kThreads, 1) mttkrp_tc_kernel(const TcArgs a) 
     // ahead (pf*), further modes when the product is formed.
     float qhc[RPT], qlc[RPT];
     float pf0[RPT], pf0l[RPT], pf1[RPT], pf1l[RPT];
-    auto load_raw = [&](const int (&ix)[kMaxModes - 2]) {
+    auto load_raw = [&](const int (&ix)[QM]) {
 #pragma unroll
       for (int rr = 0; rr < RPT; ++rr) {
         pf0[rr] = pf1[rr] = 1.f;
@@ -598,7 +601,7 @@ __global__ void __launch_bounds__(kThreads, 1) mttkrp_tc_kernel(const TcArgs a) 
         }
       }
     };
-    auto form_q = [&](const int (&ix)[kMaxModes - 2]) {
+    auto form_q = [&](const int (&ix)[QM]) {
 #pragma unroll
       for (int rr = 0; rr < RPT; ++rr) {
         float qh = 1.f, ql = 0.f;
@@ -611,7 +614,7 @@ __global__ void __launch_bounds__(kThreads, 1) mttkrp_tc_kernel(const TcArgs a) 
             qh = pf0[rr] * pf1[rr];
           }
 #pragma unroll
-          for (int t = 2; t < kMaxModes - 2; ++t) {
+          for (int t = 2; t < QM; ++t) {
             if (t < a.nq) {
               const int64_t idx = (int64_t)crow[rr] * a.qpad[t] + ix[t];
               const float bh = __ldg(a.UTq[t] + idx);
@@ -713,15 +716,15 @@ __global__ void __launch_bounds__(kThreads, 1) mttkrp_tc_kernel(const TcArgs a) 
     for (; it < stop && ok; ++it) {
       // next k-step's indices; on a carry fetch its factor entries now
       int ia_n = ia + BK;
-      int iq_n[kMaxModes - 2];
+      int iq_n[QM];
 #pragma unroll
-      for (int t = 0; t < kMaxModes - 2; ++t) iq_n[t] = iq[t];
+      for (int t = 0; t < QM; ++t) iq_n[t] = iq[t];
       bool wrap = false;
       while (ia_n >= a.Ia_pad) {
         ia_n -= a.Ia_pad;
         wrap = true;
 #pragma unroll
-        for (int t = 0; t < kMaxModes - 2; ++t) {
+        for (int t = 0; t < QM; ++t) {
           if (t < a.nq) {
             if (++iq_n[t] < a.qdims[t]) break;
             iq_n[t] = 0;
@@ -836,7 +839,7 @@ __global__ void __launch_bounds__(kThreads, 1) mttkrp_tc_kernel(const TcArgs a) 
       jcur += BK;
       ia = ia_n;
 #pragma unroll
-      for (int t = 0; t < kMaxModes - 2; ++t) iq[t] = iq_n[t];
+      for (int t = 0; t < QM; ++t) iq[t] = iq_n[t];
       if (++s == S) {
         s = 0;
         ph ^= 1u;
@@ -893,20 +896,30 @@ struct CfgExact {
 
 // The limit is per kernel and process-wide: only ever raise it, so that a
 // handle needing less never lowers it under another handle.
-template <class Cfg>
-cudaError_t set_smem_cfg(size_t smem) {
+template <class Cfg, int QM>
+cudaError_t set_smem_cfg1(size_t smem) {
   cudaFuncAttributes fa;
-  const cudaError_t e = cudaFuncGetAttributes(&fa, mttkrp_tc_kernel<Cfg>);
+  const cudaError_t e = cudaFuncGetAttributes(&fa, mttkrp_tc_kernel<Cfg, QM>);
   if (e != cudaSuccess) return e;
   if ((size_t)fa.maxDynamicSharedSizeBytes >= smem) return cudaSuccess;
-  return cudaFuncSetAttribute(mttkrp_tc_kernel<Cfg>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  return cudaFuncSetAttribute(mttkrp_tc_kernel<Cfg, QM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+template <class Cfg>
+cudaError_t set_smem_cfg(size_t smem) {
+  const cudaError_t e = set_smem_cfg1<Cfg, 2>(smem);
+  if (e != cudaSuccess) return e;
+  return set_smem_cfg1<Cfg, kMaxModes - 2>(smem);
 }
 
 template <class Cfg>
 cudaError_t launch_cfg(const TcPlan& p, const TcArgs& a, cudaStream_t s) {
   const size_t smem = tc_smem_bytes(p);
   dim3 grid((unsigned)p.tiles_c, (unsigned)p.tiles_n, (unsigned)p.splits);
-  mttkrp_tc_kernel<Cfg><<<grid, kThreads, smem, s>>>(a);
+  if (a.nq <= 2)
+    mttkrp_tc_kernel<Cfg, 2><<<grid, kThreads, smem, s>>>(a);
+  else
+    mttkrp_tc_kernel<Cfg, kMaxModes - 2><<<grid, kThreads, smem, s>>>(a);
   return cudaGetLastError();
 }
 
