@@ -195,6 +195,48 @@ jkcals_status make_tc_plan(jkcals_ctx* h) {
     p.tiles_c = (h->C + 127) / 128;
     p.tiles_n = (int)((I + p.BN - 1) / p.BN);
     if (tc::build_mma_list(prec, p) != JKCALS_OK) return fail(JKCALS_ERR_UNSUPPORTED, "accumulators exceed TMEM");
+    p.tts = 0;
+    p.nkt_a = p.n_o = p.o_per_cta = 0;
+    p.nbuf = 1;
+    if (exact && p.BN <= 64) {
+      // Two-step form: a narrow mode would reuse each Khatri-Rao entry only BN
+      // times; with the largest other mode as a (long exact chains per o) the
+      // tensor cores take U_a^T directly and the drain applies Q(c, o).
+      int amax = -1;
+      for (int k = 0; k < h->N; ++k)
+        if (k != n && (amax < 0 || h->dims[k] > h->dims[amax])) amax = k;
+      const int64_t iap = round_up(h->dims[amax], bk);
+      if (h->dims[amax] >= 128 && iap <= tc::kExactChainMax) {
+        p.tts = 1;
+        p.a_mode = amax;
+        p.Ia_pad = (int)iap;
+        p.n_o = (int)(h->J[n] / h->dims[amax]);
+        p.nkt_a = (int)(iap / bk);
+        p.Jp = iap * p.n_o;
+        p.nbuf = 2 * p.tmem_cols <= 512 ? 2 : 1;
+        p.tmem_cols *= p.nbuf;
+        p.ua_smem = 0;
+        p.ua_parts = 0;
+        p.ua_stride = 0;
+        p.stages = 2;
+        if (tc::tc_smem_bytes(p) > kSmemOptin) return fail(JKCALS_ERR_UNSUPPORTED, "two-step tile does not fit");
+        while (p.stages < 4) {
+          ++p.stages;
+          if (tc::tc_smem_bytes(p) > kSmemOptin) {
+            --p.stages;
+            break;
+          }
+        }
+        p.nkt = (int64_t)p.n_o * p.nkt_a;
+        const int64_t base = (int64_t)p.tiles_c * p.tiles_n;
+        const int64_t want = h->opt.splits > 0 ? h->opt.splits : std::max<int64_t>(1, h->num_sms / base);
+        p.o_per_cta = (int)((p.n_o + want - 1) / want);
+        p.splits = (p.n_o + p.o_per_cta - 1) / p.o_per_cta;
+        p.kchunk = (int64_t)p.o_per_cta * iap;
+        if (p.splits > 65535) return fail(JKCALS_ERR_UNSUPPORTED, "grid too large");
+        continue;
+      }
+    }
     // Shared memory: the mode-a factor rows of the CTA's 128 columns (FP32 hi,
     // BF16 lo) staged once when they fit beside two pipeline stages; then as
     // many stages as fit, up to 4.
@@ -338,6 +380,13 @@ jkcals_status enqueue_mttkrp(jkcals_ctx* h, int n, double* const* U, float* cons
   a.rowexp = h->rowexp[n];
   a.ua_smem = p.ua_smem;
   a.ua_stride = p.ua_stride;
+  a.At = static_cast<const unsigned char*>(h->At);
+  a.nkt_a = p.nkt_a;
+  a.n_o = p.n_o;
+  a.o_per_cta = p.o_per_cta;
+  a.nbuf = p.nbuf;
+  a.Ia = (int)h->dims[p.a_mode];
+  a.ut_stride_a = h->Ipad[p.a_mode];
   JK_CUDA(h, tc::launch_mttkrp_tc(h->opt.precision, p, a, h->stream));
   return JKCALS_OK;
 }
@@ -453,7 +502,14 @@ jkcals_status check_device_error(jkcals_ctx* h) {
 // Set the split-K factor of mode n's MTTKRP to about S (clamped to the
 // column count).
 void set_mode_splits(jkcals_ctx* h, int n, int64_t S) {
-  if (h->tc) {
+  if (h->tc && h->tcplan[n].tts) {
+    // two-step form: whole o values per split
+    tc::TcPlan& p = h->tcplan[n];
+    S = std::max<int64_t>(1, std::min<int64_t>(S, p.n_o));
+    p.o_per_cta = (int)((p.n_o + S - 1) / S);
+    p.splits = (p.n_o + p.o_per_cta - 1) / p.o_per_cta;
+    p.kchunk = (int64_t)p.o_per_cta * p.Ia_pad;
+  } else if (h->tc) {
     tc::TcPlan& p = h->tcplan[n];
     const int64_t bk = tc::form_bk(h->opt.precision);
     S = std::max<int64_t>(1, std::min<int64_t>(S, p.nkt));
@@ -636,6 +692,9 @@ jkcals_status create_impl(jkcals_ctx* h, const void* T, int T_dtype, const int32
   if (h->tc) {
     JK_TRY(make_tc_plan(h));
     const int chunk = tc::form_chunk(h->opt.precision);
+    size_t at_bytes = 0;
+    for (int n = 0; n < N; ++n) at_bytes = std::max(at_bytes, tc::tts_a_bytes(h->tcplan[n]));
+    if (at_bytes > 0) JK_TRY(dalloc(h, &h->At, at_bytes));
     for (int n = 0; n < N; ++n) {
       const tc::TcPlan& p = h->tcplan[n];
       JK_TRY(dalloc(h, &h->Tt[n], (size_t)p.tiles_n * p.nkt * p.nsplit * p.BN * p.row_bytes));

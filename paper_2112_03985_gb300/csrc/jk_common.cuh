@@ -89,6 +89,13 @@ struct TcPlan {
   int ua_smem;     // 1: the CTA keeps its 128 factor rows of mode a (hi, lo) in shared memory
   int ua_stride;   // floats per staged FP32 row (Ia_pad plus a bank skew)
   int ua_parts;    // staged copies: 1 (FP32 hi) or 2 (plus BF16 lo)
+  // two-step exact form (narrow modes): Y_o = U_a^T T_(n)(:, o)^T per index o of
+  // the remaining modes on the tensor cores, scaled by Q(c, o) and summed in the drain
+  int tts;         // 1: this mode runs the two-step form
+  int nkt_a;       // k-steps per o (Ia_pad / BK)
+  int n_o;         // values of o
+  int o_per_cta;   // o values per CTA (one split)
+  int nbuf;        // TMEM accumulator sets (2: the next o accumulates while one drains)
   MmaList mma;     // MMAs per K slice
 };
 }  // namespace tc
@@ -159,6 +166,7 @@ struct jkcals_ctx {
   // tensor-core forms (precision != JKCALS_FP64)
   bool tc = false;
   void* Tt[jk::kMaxModes] = {nullptr};  // split, padded, pre-tiled unfoldings
+  void* At = nullptr;                    // two-step modes: sliced, pre-tiled U_a^T (rewritten per launch)
   float* UT[jk::kMaxModes] = {nullptr};      // C x Ipad FP32 transposed factors
   float* gUT[jk::kMaxModes] = {nullptr};     // same, for the gradient's factor set
   float* UTlo[jk::kMaxModes] = {nullptr};    // exact-chain form: low parts, U = UT + UTlo

@@ -894,6 +894,331 @@ struct CfgExact {
   static constexpr bool exact = true;
 };
 
+// ---- two-step exact form ----------------------------------------------------------
+// For a mode whose rows fit one narrow N tile (BN <= 64) each Khatri-Rao entry would
+// be reused only BN times, so building the KRP bounds the kernel.  Instead, with a
+// the largest other mode and o the index of the remaining ones,
+//   Mbar_n^T(c, i) = sum_o Q(c, o) Y_o(c, i),   Y_o = U_a^T (C x I_a) . T_(n)(:, o)^T,
+// Q(c, o) the product of the remaining modes' factor entries of column c (the
+// Khatri-Rao factorisation of Eq. MTTKRP taken one mode at a time).  Each Y_o is
+// one exact-chain GEMM over I_a <= 1024 columns: A = U_a^T sliced like T (4 BF16
+// slices on the row's power-of-two grid, sliced once per launch into stage
+// images read by TMA), B = the pre-tiled unfolding as for the other forms.  The
+// epilogue warps drain each o's accumulators (double-buffered in TMEM, so the
+// next o accumulates meanwhile), combine the levels into an FP32 pair, multiply
+// by Q(c, o) as an FP32 pair (error-free products) and add into per-thread
+// double-float sums; the column powers of two are applied once at the end.
+
+// exponent E with max |U_a(:, c)| < 2^E (0 for an all-zero column)
+__device__ __forceinline__ int col_exponent(float cmax) {
+  if (!(cmax > 0.f)) return 0;
+  int e;
+  frexpf(cmax, &e);
+  return e < -110 ? -110 : (e > 110 ? 110 : e);
+}
+
+// A stage images of U_a^T: for 128-row tile tc and k-step ks (columns ia in
+// [32 ks, 32 ks + 32) of the padded mode a), 4 parts of 128 rows x 64 bytes in
+// the 64-byte swizzle, the layout the producers of the one-step form write.
+__global__ void slice_a_kernel(const float* __restrict__ UT, const float* __restrict__ UT_lo, int64_t ut_stride,
+                               int Ia, int Ia_pad, const float* __restrict__ cmax, int C, int tiles_c,
+                               unsigned char* __restrict__ At) {
+  constexpr int ROW = CfgExact::row_bytes, BK = ROW / 2;
+  const int chunks = Ia_pad / 8;
+  const int nkt_a = Ia_pad / BK;
+  const int64_t total = (int64_t)tiles_c * kRowsM * chunks;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int c = (int)(e / chunks);
+    const int ch = (int)(e - (int64_t)c * chunks);
+    const int ia0 = ch * 8;
+    float uh[8], ul[8];
+    float sc = 0.f;
+    if (c < C) sc = pow2f(kSliceBits - col_exponent(__ldg(cmax + c)));
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const bool in = c < C && ia0 + k < Ia;
+      uh[k] = in ? __ldg(UT + (int64_t)c * ut_stride + ia0 + k) : 0.f;
+      ul[k] = in ? __ldg(UT_lo + (int64_t)c * ut_stride + ia0 + k) : 0.f;
+    }
+    const f2 s2 = f2_pack(sc, sc), ns2 = f2_pack(-sc, -sc), z2 = f2_pack(0.f, 0.f);
+    uint32_t w[4][4];
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+      uint32_t ws[4];
+      exact_slices2(f2_pack(uh[2 * p], uh[2 * p + 1]), f2_pack(ul[2 * p], ul[2 * p + 1]), s2, ns2, z2, ws);
+#pragma unroll
+      for (int t = 0; t < 4; ++t) w[t][p] = ws[t];
+    }
+    const int tc = c / kRowsM, m = c - tc * kRowsM, ks = ia0 / BK, q = (ia0 - ks * BK) / 8;
+    unsigned char* img = At + ((int64_t)tc * nkt_a + ks) * 4 * (kRowsM * ROW);
+    const uint32_t off = (uint32_t)(m >> 3) * (8u * ROW) + (uint32_t)(m & 7) * ROW + (uint32_t)((q ^ ((m >> 1) & 3)) << 4);
+#pragma unroll
+    for (int t = 0; t < 4; ++t)
+      *reinterpret_cast<uint4*>(img + t * (kRowsM * ROW) + off) = make_uint4(w[t][0], w[t][1], w[t][2], w[t][3]);
+  }
+}
+
+template <int QM>
+__global__ void __launch_bounds__(kThreads, 1) mttkrp_tts_kernel(const TcArgs a) {
+  using Cfg = CfgExact;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* smem =
+      reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  constexpr int NS = Cfg::nsplit;
+  constexpr int ROW = Cfg::row_bytes;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t a_bytes = kRowsM * ROW;
+  const uint32_t b_bytes = (uint32_t)a.BN * ROW;
+  const uint32_t a_stage = NS * a_bytes, b_stage = NS * b_bytes;
+  const uint32_t stage_bytes = a_stage + b_stage;   // a multiple of 1024
+  const int S = a.stages;
+  unsigned char* ring = smem;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(ring + (size_t)S * stage_bytes);
+  uint64_t* full = bars;                  // stage loaded (the TMA arrival and its bytes)
+  uint64_t* empty = bars + S;             // stage consumed (the MMAs' commit)
+  uint64_t* accum = bars + 2 * S;         // [2] one o's MMAs complete in accumulator set b
+  uint64_t* tmem_empty = accum + 2;       // [2] the epilogue warps drained set b
+  uint64_t* drain = accum + 4;            // abort path: the MMAs issued so far are complete
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accum + 5);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  int* srowexp = const_cast<int*>(abort_flag + 1);   // BN row exponents of this N tile
+
+  const int c0 = blockIdx.x * kRowsM;
+  const int n0 = blockIdx.y * a.BN;
+  const int o0 = blockIdx.z * a.o_per_cta;
+  const int o1 = o0 + a.o_per_cta < a.n_o ? o0 + a.o_per_cta : a.n_o;
+  const int nseg = o1 > o0 ? o1 - o0 : 0;
+  const int nkt_a = a.nkt_a;
+  const int nk = nseg * nkt_a;
+  const int nbuf = a.nbuf;
+  const uint32_t set_cols = (uint32_t)(a.nlev * a.lstride);   // columns of one accumulator set
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(&accum[0], 1);
+    mbar_init(&accum[1], 1);
+    mbar_init(&tmem_empty[0], kEpilogueWarps);
+    mbar_init(&tmem_empty[1], kEpilogueWarps);
+    mbar_init(drain, 1);
+    *abort_flag = 0;
+    fence_barrier_init();
+  }
+  if (warp == 1) tmem_alloc(tmem_slot, (uint32_t)a.tmem_cols);
+  if ((int)threadIdx.x < a.BN) {
+    const int64_t i = (int64_t)n0 + threadIdx.x;
+    srowexp[threadIdx.x] = i < a.I ? __ldg(a.rowexp + i) : 0;
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    // ---------------- TMA: lane s loads ring stage s (A image and B image) --------
+    if (lane < S) {
+      int issued = 0;
+      const unsigned char* srcb = a.Tt + ((int64_t)blockIdx.y * a.nkt + (int64_t)o0 * nkt_a) * (int64_t)b_stage;
+      const unsigned char* srca = a.At + (int64_t)blockIdx.x * nkt_a * (int64_t)a_stage;
+      unsigned char* dst = ring + (size_t)lane * stage_bytes;
+      uint32_t ph = 0;
+      int kk = lane % (nkt_a > 0 ? nkt_a : 1);   // k-step within its o
+      for (int it = lane; it < nk; it += S, ph ^= 1u) {
+        if (!wait_bounded(&empty[lane], ph ^ 1u, abort_flag, a.err, 1)) break;
+        mbar_arrive_expect_tx(&full[lane], a_stage + b_stage);
+        bulk_load(dst, srca + (int64_t)kk * a_stage, a_stage, &full[lane]);
+        bulk_load(dst + a_stage, srcb + (int64_t)it * b_stage, b_stage, &full[lane]);
+        issued = it + 1;
+        kk += S;
+        while (kk >= nkt_a) kk -= nkt_a;
+      }
+      if (*abort_flag && issued > 0) {
+        const uint64_t t0 = global_ns();
+        while (global_ns() - t0 < 200000ull) {
+        }
+      }
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer ----------------------------------------------------
+    if (lane == 0) {
+      const uint64_t desc0 = smem_desc<ROW>(smem_u32(ring));
+      const uint32_t L = (uint32_t)a.lstride, b16 = b_bytes >> 4;
+      uint32_t idesc[5];
+#pragma unroll
+      for (int c = 0; c < 5; ++c)
+        idesc[c] = (1u << 4) | ((uint32_t)Cfg::fmt << 7) | ((uint32_t)Cfg::fmt << 10) |
+                   (((uint32_t)(c * a.BN) >> 3) << 17) | ((uint32_t)(kRowsM >> 4) << 24);
+      const int variant = a.stack >= 4 ? 4 : a.stack;
+      bool ok = true;
+      int j = 0, kin = 0, b = 0;   // o (segment), k-step within it, accumulator set
+      uint32_t uses0 = 0, uses1 = 0;   // fills of each accumulator set so far
+      int s = 0;
+      uint32_t ph = 0;
+      for (int it = 0; it < nk && ok; ++it) {
+        if (kin == 0 && j >= nbuf) {
+          // set b is refilled once the epilogue drained its previous o
+          ok = wait_bounded(&tmem_empty[b], ((b ? uses1 : uses0) - 1u) & 1u, abort_flag, a.err, 7);
+          if (!ok) break;
+        }
+        ok = wait_bounded(&full[s], ph, abort_flag, a.err, 2);
+        if (!ok) break;
+        tc_fence_after();
+        const uint64_t ad0 = desc0 + (uint64_t)(((uint32_t)s * stage_bytes) >> 4);
+        const uint64_t bd0 = ad0 + (uint64_t)(a_stage >> 4);
+        const uint32_t td = tmem + (uint32_t)b * set_cols;
+#pragma unroll
+        for (int kq = 0; kq < ROW / 32; ++kq) {
+          const bool first = kin == 0 && kq == 0;
+          switch (variant) {
+            case 4: issue_slice<Cfg, 4, false>(td, ad0, bd0, L, b16, idesc, kq, first); break;
+            case 2: issue_slice<Cfg, 2, false>(td, ad0, bd0, L, b16, idesc, kq, first); break;
+            default: issue_slice<Cfg, 1, false>(td, ad0, bd0, L, b16, idesc, kq, first); break;
+          }
+        }
+        tc_commit(&empty[s]);
+        if (++kin == nkt_a) {
+          tc_commit(&accum[b]);   // this o complete in set b
+          kin = 0;
+          ++j;
+          if (b) ++uses1; else ++uses0;
+          b = (nbuf == 2) ? b ^ 1 : 0;
+        }
+        if (++s == S) {
+          s = 0;
+          ph ^= 1u;
+        }
+      }
+      if (!ok) {
+        tc_commit(drain);
+        wait_drain(drain, 0);
+      }
+    }
+  } else if (warp >= kEpilogueWarp0) {
+    // ---------------- epilogue: per o, scale by Q(c, o) and accumulate ---------------
+    const int quarter = warp & 3;                   // TMEM lanes 32 quarter .. + 31
+    const int grp = (warp - kEpilogueWarp0) >> 2;   // two warps per quarter split the columns
+    const int m_e = quarter * 32 + lane;
+    const int c = c0 + m_e;
+    const bool cv = c < a.C;
+    const int cc_ = cv ? c : 0;
+    const int Ec = cv ? col_exponent(__ldg(a.cmax_a + c)) : 0;
+    const float rsc = pow2f(Ec - 2 * kSliceBits);   // 2^(E_c - 14): the row part of the level scale
+    // Q(c, o) as an FP32 pair, times rsc (exact)
+    auto load_q = [&](int o, float& qh, float& ql) {
+      qh = rsc;
+      ql = 0.f;
+      int rem = o;
+#pragma unroll
+      for (int t = 0; t < QM; ++t) {
+        if (t < a.nq) {
+          const int qq = rem / a.qdims[t];
+          const int idx = rem - qq * a.qdims[t];
+          rem = qq;
+          const int64_t off = (int64_t)cc_ * a.qpad[t] + idx;
+          pair_mul(qh, ql, __ldg(a.UTq[t] + off), __ldg(a.UTq_lo[t] + off));
+        }
+      }
+    };
+    // this warp's columns: 16-column slices cc = 16 grp + 32 k (BN <= 64: at most 2)
+    float acc_h[32], acc_l[32];
+#pragma unroll
+    for (int r = 0; r < 32; ++r) acc_h[r] = acc_l[r] = 0.f;
+    bool ok = true;
+    float qh = 0.f, ql = 0.f;
+    if (nseg > 0) load_q(o0, qh, ql);
+    const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16);
+    const uint32_t L = (uint32_t)a.lstride;
+    int b = 0;
+    uint32_t uses0 = 0, uses1 = 0;   // drains of each accumulator set so far
+    for (int j = 0; j < nseg; ++j) {
+      bool have = ok && wait_sleepy(&accum[b], (b ? uses1 : uses0) & 1u, abort_flag, a.err, 5);
+      have = __all_sync(0xffffffffu, have);
+      if (!have) {
+        ok = false;
+        break;
+      }
+      tc_fence_after();
+      float qhn = 0.f, qln = 0.f;
+      if (j + 1 < nseg) load_q(o0 + j + 1, qhn, qln);   // in flight during this drain
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        const int cc = 16 * grp + 32 * k;
+        if (cc < a.BN) {
+          uint32_t v0[32], v1[32], v2[32], v3[32];
+          const uint32_t col = lane_base + (uint32_t)b * set_cols + (uint32_t)cc;
+          tmem_ld16(col, v0);
+          tmem_ld16(col + L, v1);
+          tmem_ld16(col + 2 * L, v2);
+          tmem_ld16(col + 3 * L, v3);
+          tmem_ld_wait();
+#pragma unroll
+          for (int r = 0; r < 16; ++r) {
+            // levels as an FP32 pair (TwoSum; levels 0 and 1 exact, 2 and 3 small)
+            const float l0 = __uint_as_float(v0[r]), l1 = __uint_as_float(v1[r]);
+            const float l2 = __uint_as_float(v2[r]) + __uint_as_float(v3[r]);
+            const float s = __fadd_rn(l0, l1);
+            const float bb = __fsub_rn(s, l0);
+            const float e1 = __fadd_rn(__fsub_rn(l0, __fsub_rn(s, bb)), __fsub_rn(l1, bb));
+            const float t = __fadd_rn(s, l2);
+            const float b2 = __fsub_rn(t, s);
+            const float e2 = __fadd_rn(__fsub_rn(s, __fsub_rn(t, b2)), __fsub_rn(l2, b2));
+            const float lo0 = __fadd_rn(e1, e2);
+            const float hi = __fadd_rn(t, lo0);
+            const float lo = __fsub_rn(lo0, __fsub_rn(hi, t));
+            // times Q (pair): error-free leading product, cross terms
+            const float p = __fmul_rn(hi, qh);
+            const float pe = __fmaf_rn(lo, qh, __fmaf_rn(hi, ql, __fmaf_rn(hi, qh, -p)));
+            // accumulate (double-float)
+            const int idx = 16 * k + r;
+            const float sh = __fadd_rn(acc_h[idx], p);
+            const float bv = __fsub_rn(sh, acc_h[idx]);
+            const float eh = __fadd_rn(__fsub_rn(acc_h[idx], __fsub_rn(sh, bv)), __fsub_rn(p, bv));
+            const float el = __fadd_rn(eh, __fadd_rn(acc_l[idx], pe));
+            acc_h[idx] = __fadd_rn(sh, el);
+            acc_l[idx] = __fsub_rn(el, __fsub_rn(acc_h[idx], sh));
+          }
+        }
+      }
+      // this warp's TMEM reads are complete: release set b
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&tmem_empty[b]);
+      if (b) ++uses1; else ++uses0;
+      b = (nbuf == 2) ? b ^ 1 : 0;
+      qh = qhn;
+      ql = qln;
+    }
+    // the column powers of two, then this split's partial (the consumer adds hi + lo)
+    float2* out2 = reinterpret_cast<float2*>(a.part) + (int64_t)blockIdx.z * a.I * a.C;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const int cc = 16 * grp + 32 * k;
+      if (cc < a.BN) {
+#pragma unroll
+        for (int r = 0; r < 16; ++r) {
+          const int64_t i = (int64_t)n0 + cc + r;
+          if (i < a.I && cv) {
+            int kx = srowexp[cc + r];
+            kx = kx < -120 ? -120 : (kx > 120 ? 120 : kx);
+            const float sx = pow2f(kx);
+            const int idx = 16 * k + r;
+            out2[i * a.C + c] = ok ? make_float2(acc_h[idx] * sx, acc_l[idx] * sx) : make_float2(0.f, 0.f);
+          }
+        }
+      }
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem, (uint32_t)a.tmem_cols);
+  }
+}
+
 // The limit is per kernel and process-wide: only ever raise it, so that a
 // handle needing less never lowers it under another handle.
 template <class Cfg, int QM>
@@ -910,6 +1235,33 @@ cudaError_t set_smem_cfg(size_t smem) {
   const cudaError_t e = set_smem_cfg1<Cfg, 2>(smem);
   if (e != cudaSuccess) return e;
   return set_smem_cfg1<Cfg, kMaxModes - 2>(smem);
+}
+
+template <int QM>
+cudaError_t set_smem_tts1(size_t smem) {
+  cudaFuncAttributes fa;
+  const cudaError_t e = cudaFuncGetAttributes(&fa, mttkrp_tts_kernel<QM>);
+  if (e != cudaSuccess) return e;
+  if ((size_t)fa.maxDynamicSharedSizeBytes >= smem) return cudaSuccess;
+  return cudaFuncSetAttribute(mttkrp_tts_kernel<QM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+cudaError_t launch_tts(const TcPlan& p, const TcArgs& a, cudaStream_t s) {
+  // slice U_a^T into the A stage images, then the two-step GEMMs
+  const int64_t work = (int64_t)p.tiles_c * kRowsM * (p.Ia_pad / 8);
+  int64_t blocks = (work + 255) / 256;
+  if (blocks > 4096) blocks = 4096;
+  slice_a_kernel<<<(unsigned)blocks, 256, 0, s>>>(a.UTa, a.UTa_lo, a.ut_stride_a, a.Ia, p.Ia_pad, a.cmax_a, a.C,
+                                                  p.tiles_c, const_cast<unsigned char*>(a.At));
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const size_t smem = tc_smem_bytes(p);
+  dim3 grid((unsigned)p.tiles_c, (unsigned)p.tiles_n, (unsigned)p.splits);
+  if (a.nq <= 2)
+    mttkrp_tts_kernel<2><<<grid, kThreads, smem, s>>>(a);
+  else
+    mttkrp_tts_kernel<kMaxModes - 2><<<grid, kThreads, smem, s>>>(a);
+  return cudaGetLastError();
 }
 
 template <class Cfg>
@@ -999,8 +1351,15 @@ size_t tc_smem_bytes(const TcPlan& p) {
   const size_t row = (size_t)p.row_bytes;
   const size_t a_stage = (size_t)p.nsplit * kRowsM * row;
   const size_t b_stage = (size_t)p.nsplit * p.BN * row;
+  if (p.tts)   // ring | barriers (2 S + 5) | TMEM slot, abort word | row exponents
+    return 1024 + (size_t)p.stages * (a_stage + b_stage) + (2 * p.stages + 5) * 8 + 16 + 4 * (size_t)p.BN;
   return 1024 /*alignment slack*/ + (size_t)p.stages * (a_stage + b_stage) + tc_ua_bytes(p) + (2 * p.stages + 3) * 8 +
          16 + 4 * (size_t)p.BN;
+}
+
+size_t tts_a_bytes(const TcPlan& p) {
+  if (!p.tts) return 0;
+  return (size_t)p.tiles_c * p.nkt_a * p.nsplit * kRowsM * p.row_bytes;
 }
 
 cudaError_t prepare_mttkrp_tc(int precision, size_t max_smem) {
@@ -1009,7 +1368,13 @@ cudaError_t prepare_mttkrp_tc(int precision, size_t max_smem) {
     case JKCALS_3XTF32: return set_smem_cfg<Cfg3xTF32>(max_smem);
     case JKCALS_BF16: return set_smem_cfg<CfgBF16>(max_smem);
     case JKCALS_SPLIT_BF16: return set_smem_cfg<CfgBF16x3>(max_smem);
-    case JKCALS_EXACT_BF16: return set_smem_cfg<CfgExact>(max_smem);
+    case JKCALS_EXACT_BF16: {
+      const cudaError_t e = set_smem_cfg<CfgExact>(max_smem);
+      if (e != cudaSuccess) return e;
+      const cudaError_t e2 = set_smem_tts1<2>(max_smem);
+      if (e2 != cudaSuccess) return e2;
+      return set_smem_tts1<kMaxModes - 2>(max_smem);
+    }
     default: return cudaErrorInvalidValue;
   }
 }
@@ -1020,7 +1385,7 @@ cudaError_t launch_mttkrp_tc(int precision, const TcPlan& p, const TcArgs& a, cu
     case JKCALS_3XTF32: return launch_cfg<Cfg3xTF32>(p, a, s);
     case JKCALS_BF16: return launch_cfg<CfgBF16>(p, a, s);
     case JKCALS_SPLIT_BF16: return launch_cfg<CfgBF16x3>(p, a, s);
-    case JKCALS_EXACT_BF16: return launch_cfg<CfgExact>(p, a, s);
+    case JKCALS_EXACT_BF16: return p.tts ? launch_tts(p, a, s) : launch_cfg<CfgExact>(p, a, s);
     default: return cudaErrorInvalidValue;
   }
 }

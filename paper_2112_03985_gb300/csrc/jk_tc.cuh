@@ -53,6 +53,11 @@ struct TcArgs {
   const int* rowexp;               // I_n: F_i of this mode's unfolding
   int ua_smem;                     // stage the 128 rows of UTa (and UTa_lo) in shared memory
   int ua_stride;                   // floats per staged FP32 row (BF16 low rows: Ia_pad elements)
+  // two-step exact form only (TcPlan::tts):
+  const unsigned char* At;         // sliced, pre-tiled U_a^T: per 128-row tile and k-step one A stage image
+  int nkt_a, n_o, o_per_cta, nbuf;
+  int Ia;                          // size of mode a
+  int64_t ut_stride_a;             // row stride of UTa / UTa_lo (floats)
 };
 
 int form_nsplit(int precision);
@@ -69,6 +74,8 @@ int build_mma_list(int precision, TcPlan& p);
 // Raise the kernel's dynamic shared-memory limit (call once, outside stream capture).
 cudaError_t prepare_mttkrp_tc(int precision, size_t max_smem);
 cudaError_t launch_mttkrp_tc(int precision, const TcPlan& p, const TcArgs& a, cudaStream_t s);
+// Bytes of the A images of a two-step plan (tiles_c x nkt_a stage images).
+size_t tts_a_bytes(const TcPlan& p);
 
 // create-time conversions (jk_tc_prep.cu)
 // rowexp[i] = smallest F with max_j |Tn64(i, j)| < 2^F (0 for an all-zero row)
