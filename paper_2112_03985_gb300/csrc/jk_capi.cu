@@ -198,15 +198,21 @@ jkcals_status make_tc_plan(jkcals_ctx* h) {
     p.tts = 0;
     p.nkt_a = p.n_o = p.o_per_cta = 0;
     p.nbuf = 1;
-    if (exact && p.BN <= 64) {
+    if (exact && I <= 128) {
       // Two-step form: a narrow mode would reuse each Khatri-Rao entry only BN
       // times; with the largest other mode as a (long exact chains per o) the
-      // tensor cores take U_a^T directly and the drain applies Q(c, o).
+      // tensor cores take U_a^T directly and the drain applies Q(c, o).  N
+      // tiles of at most 64 rows (two accumulator sets fit TMEM).
       int amax = -1;
       for (int k = 0; k < h->N; ++k)
         if (k != n && (amax < 0 || h->dims[k] > h->dims[amax])) amax = k;
       const int64_t iap = round_up(h->dims[amax], bk);
       if (h->dims[amax] >= 128 && iap <= tc::kExactChainMax) {
+        if (p.BN > 64) {
+          p.BN = 64;
+          p.tiles_n = (int)((I + p.BN - 1) / p.BN);
+          if (tc::build_mma_list(prec, p) != JKCALS_OK) return fail(JKCALS_ERR_UNSUPPORTED, "accumulators exceed TMEM");
+        }
         p.tts = 1;
         p.a_mode = amax;
         p.Ia_pad = (int)iap;
