@@ -39,6 +39,11 @@ SHAPES = [
     ("two N tiles 300x9x7 R2", lambda: _w((300, 9, 7), 2, seed=4)),
     ("delete-3 mixed ranks 12x21x10", lambda: _w((12, 21, 10), 2, d=3, seed=5, ranks=[1, 5, 2, 7])),
     ("long chains 8x70x60 R2", lambda: _w((8, 70, 60), 2, seed=6)),
+    # two-step form (modes of <= 128 rows whose largest other mode has >= 128):
+    # two N tiles with a ragged second one, o over one mode
+    ("two-step 150x90x7 R3", lambda: _w((150, 90, 7), 3, seed=7)),
+    # two-step with o over two modes (Q a product of two factor entries), n_hat = 1
+    ("two-step 4-way 140x20x12x9", lambda: _w((140, 20, 12, 9), 2, n_hat=1, seed=8)),
 ]
 
 
