@@ -100,41 +100,21 @@ __global__ void __launch_bounds__(NT, FIXED ? 4 : 2) update_fused_kernel(UpdateA
   __shared__ int spd_ok;
   __shared__ int colmax[RMAX];   // FP32 bit patterns of max |hi| per column (non-negative: int order)
 
-  for (int p = tid; p < R * R; p += NT) {
-    double h = 1.0;
-    for (int k = 0; k < a.N; ++k)
-      if (k != a.n) h *= a.gram[k][go + p];
-    L[p / R][p % R] = h;
-    Hc[p] = h;
-  }
-  if (tid == 0) spd_ok = 1;
   if (tid < RMAX) colmax[tid] = 0;
-  // this block's rows of Mbar_n into X, their loads in flight together with
-  // those of the Grams (a few rows per thread issued before any store)
-  {
-    constexpr int kLd = RMAX <= 8 ? 4 : 1;
-    for (int64_t i0 = tid; i0 < I; i0 += (int64_t)kLd * NT) {
-      double v[kLd][RMAX];
-#pragma unroll
-      for (int u = 0; u < kLd; ++u) {
-        const int64_t i = i0 + (int64_t)u * NT;
-#pragma unroll
-        for (int r = 0; r < RMAX; ++r) v[u][r] = (i < I && r < R) ? M[i * a.C + off + r] : 0.0;
-      }
-#pragma unroll
-      for (int u = 0; u < kLd; ++u) {
-        const int64_t i = i0 + (int64_t)u * NT;
-        if (i < I) {
-#pragma unroll
-          for (int r = 0; r < RMAX; ++r)
-            if (r < R) X[i * R + r] = v[u][r];
-        }
-      }
-    }
-  }
-  __syncthreads();
-  if (tid < 32) {
+  const int warp = tid >> 5;
+  if (warp == 0) {
+    // warp 0: H (its R^2 entries over the lanes), then its Cholesky factor,
+    // while the other warps load the block's rows of Mbar_n
     const int lane = tid;
+    if (lane == 0) spd_ok = 1;
+    for (int p = lane; p < R * R; p += 32) {
+      double h = 1.0;
+      for (int k = 0; k < a.N; ++k)
+        if (k != a.n) h *= a.gram[k][go + p];
+      L[p / R][p % R] = h;
+      Hc[p] = h;
+    }
+    __syncwarp();
     for (int j = 0; j < R; ++j) {
       if (lane == 0) {
         double d = L[j][j];
@@ -158,6 +138,29 @@ __global__ void __launch_bounds__(NT, FIXED ? 4 : 2) update_fused_kernel(UpdateA
         L[i][j] = v * invd[j];
       }
       __syncwarp();
+    }
+  } else {
+    // warps 1.. : this block's rows of Mbar_n into X (a few rows per thread
+    // with their loads issued before any store)
+    constexpr int kLd = RMAX <= 8 ? 4 : 1;
+    constexpr int NL = NT - 32;
+    for (int64_t i0 = tid - 32; i0 < I; i0 += (int64_t)kLd * NL) {
+      double v[kLd][RMAX];
+#pragma unroll
+      for (int u = 0; u < kLd; ++u) {
+        const int64_t i = i0 + (int64_t)u * NL;
+#pragma unroll
+        for (int r = 0; r < RMAX; ++r) v[u][r] = (i < I && r < R) ? M[i * a.C + off + r] : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < kLd; ++u) {
+        const int64_t i = i0 + (int64_t)u * NL;
+        if (i < I) {
+#pragma unroll
+          for (int r = 0; r < RMAX; ++r)
+            if (r < R) X[i * R + r] = v[u][r];
+        }
+      }
     }
   }
   __syncthreads();
@@ -300,19 +303,20 @@ __global__ void __launch_bounds__(NT, FIXED ? 4 : 2) update_fused_kernel(UpdateA
   for (int p = tid; p < R * R; p += NT) a.gram_n[go + p] = G[p / R][p % R];
   if (!last) return;
 
-  // e_g = ||T_{-g}||^2 + sum(H * G) - 2 sum(x * m)
-  __syncthreads();
+  // e_g = ||T_{-g}||^2 + sum(H * G) - 2 sum(x * m): warp sums, then the warps'
+  // partials in order (fixed order: deterministic)
   double hg = 0.0;
   for (int p = tid; p < R * R; p += NT) hg = fma(Hc[p], G[p / R][p % R], hg);
-  red[tid] = hg - 2.0 * fit;
+  double v = hg - 2.0 * fit;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((tid & 31) == 0) red[warp] = v;
   __syncthreads();
-  for (int w = NT / 2; w > 0; w >>= 1) {
-    if (tid < w) red[tid] += red[tid + w];
-    __syncthreads();
-  }
   if (tid == 0) {
+    double acc = 0.0;
+    for (int w = 0; w < NT / 32; ++w) acc += red[w];
     const double nt = a.normT2[g];
-    const double e = nt + red[0];
+    const double e = nt + acc;
     a.loss_last[g] = e;
     if (a.loss_hist != nullptr && sweep < a.loss_cap) a.loss_hist[(int64_t)sweep * a.K + g] = e;
     const double tol = *a.tol;
