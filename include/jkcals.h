@@ -66,9 +66,13 @@ typedef enum {
   JKCALS_EXACT_BF16 = 5   /* exact-chain sliced BF16: every operand row is cut into four
                              7-bit integer slices on a shared power-of-two grid, stored as
                              BF16; the two leading product levels accumulate exactly in
-                             FP32 TMEM (chains <= 1024 terms), the rest in a third
-                             accumulator; chains are combined in FP64.  About FP64-level
-                             MTTKRP accuracy on the tensor cores (10 BF16 MMA passes). */
+                             FP32 TMEM (chains <= 1024 terms), the smaller levels beside
+                             them; chains are combined as FP32 pairs (double-float) and
+                             the split-K partials summed into FP64.  Modes of <= 128 rows
+                             whose largest other mode has >= 128 run a two-step variant
+                             (GEMMs against the sliced rows of that mode, scaled by the
+                             remaining modes' entries).  About FP64-level MTTKRP accuracy
+                             on the tensor cores (10 BF16 MMA passes). */
 } jkcals_prec;
 
 typedef enum { JKCALS_DTYPE_F32 = 0, JKCALS_DTYPE_F64 = 1 } jkcals_dtype;

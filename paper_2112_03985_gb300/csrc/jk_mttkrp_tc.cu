@@ -58,6 +58,10 @@
 // commit), so the MMA lane waits once per stage; one more for the accumulator.  Every wait is bounded
 // by a wall-clock limit; on expiry the CTA records an error code, stops, waits
 // (bounded) for its own TMA copies and MMAs, frees its TMEM and returns.
+//
+// The exact-chain form has a second kernel for narrow modes (mttkrp_tts_kernel,
+// further down): no Khatri-Rao producers, one GEMM per index of the remaining
+// modes, the scaling by their factor entries done in the epilogue.
 #include <cuda_bf16.h>
 
 #include "jk_common.cuh"
