@@ -2,8 +2,8 @@
 
 The reduced-precision forms accumulate in FP32 in TMEM; their error against the
 FP64 oracle grows with the length of the accumulation chain (each split-K
-chain of ~J/S terms), so the bounds below are per shape class.  They are
-reported by bench.py and in DESIGN.md; none of these forms is "at parity".
+chain of ~J/S terms), so the bounds below are per shape class.  bench.py
+reports them; none of these forms is "at parity".
 """
 import numpy as np
 import pytest
