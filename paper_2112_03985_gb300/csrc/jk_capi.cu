@@ -342,8 +342,10 @@ UpdateArgs update_args(jkcals_ctx* h, int n, const void* part, int part_kind, in
 }
 
 // Enqueue the concurrent MTTKRP of mode n for factor set (U, UT, cmax) into h->part.
+// reuse_slices: a two-step mode may reuse the U_a slices left in At by the
+// previous two-step launch of the same sweep when mode a was not updated since.
 jkcals_status enqueue_mttkrp(jkcals_ctx* h, int n, double* const* U, float* const* UT, float* const* UTlo,
-                             float* const* cmax) {
+                             float* const* cmax, bool reuse_slices = false) {
   if (!h->tc) {
     const ModePlan& p = h->plan[n];
     KrpOperands kr = krp_operands(h, n, U);
@@ -393,6 +395,7 @@ jkcals_status enqueue_mttkrp(jkcals_ctx* h, int n, double* const* U, float* cons
   a.nbuf = p.nbuf;
   a.Ia = (int)h->dims[p.a_mode];
   a.ut_stride_a = h->Ipad[p.a_mode];
+  a.skip_slice = (p.tts && reuse_slices) ? 1 : 0;
   JK_CUDA(h, tc::launch_mttkrp_tc(h->opt.precision, p, a, h->stream));
   return JKCALS_OK;
 }
@@ -417,9 +420,16 @@ jkcals_status reduce_into(jkcals_ctx* h, int n, double* out) {
 
 jkcals_status enqueue_sweep(jkcals_ctx* h) {
   int kernels = 0;
+  int sliced = -1;   // mode whose current slices At holds (two-step modes)
   for (int n = 0; n < h->N; ++n) {
+    const bool tts = h->tc && h->tcplan[n].tts;
+    const bool reuse = tts && sliced == h->tcplan[n].a_mode;
     if (h->opt.kernel_timing) JK_CUDA(h, cudaEventRecordWithFlags(h->ev_start[n], h->stream, cudaEventRecordExternal));
-    JK_TRY(enqueue_mttkrp(h, n, h->U, h->UT, h->UTlo, h->cmax));
+    JK_TRY(enqueue_mttkrp(h, n, h->U, h->UT, h->UTlo, h->cmax, reuse));
+    if (tts) {
+      sliced = h->tcplan[n].a_mode;
+      kernels += reuse ? 0 : 1;
+    }
     if (h->opt.kernel_timing) JK_CUDA(h, cudaEventRecordWithFlags(h->ev_stop[n], h->stream, cudaEventRecordExternal));
     // fixed-order split-K reduction into FP64 Mbar_n, then the per-block update
     JK_TRY(reduce_into(h, n, h->mbuf));
@@ -431,6 +441,7 @@ jkcals_status enqueue_sweep(jkcals_ctx* h) {
       JK_CUDA(h, launch_update(a, h->stream));
       kernels += 4;
     }
+    if (n == sliced) sliced = -1;   // U_a changed: the slices in At are stale
   }
   JK_CUDA(h, launch_advance_sweep(h->d_sweep_idx, h->stream));
   h->kernels_per_sweep = kernels + 1;

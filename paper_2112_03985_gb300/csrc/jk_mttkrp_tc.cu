@@ -1251,14 +1251,17 @@ cudaError_t set_smem_tts1(size_t smem) {
 }
 
 cudaError_t launch_tts(const TcPlan& p, const TcArgs& a, cudaStream_t s) {
-  // slice U_a^T into the A stage images, then the two-step GEMMs
-  const int64_t work = (int64_t)p.tiles_c * kRowsM * (p.Ia_pad / 8);
-  int64_t blocks = (work + 255) / 256;
-  if (blocks > 4096) blocks = 4096;
-  slice_a_kernel<<<(unsigned)blocks, 256, 0, s>>>(a.UTa, a.UTa_lo, a.ut_stride_a, a.Ia, p.Ia_pad, a.cmax_a, a.C,
-                                                  p.tiles_c, const_cast<unsigned char*>(a.At));
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
+  // slice U_a^T into the A stage images (unless they are current), then the
+  // two-step GEMMs
+  if (!a.skip_slice) {
+    const int64_t work = (int64_t)p.tiles_c * kRowsM * (p.Ia_pad / 8);
+    int64_t blocks = (work + 255) / 256;
+    if (blocks > 4096) blocks = 4096;
+    slice_a_kernel<<<(unsigned)blocks, 256, 0, s>>>(a.UTa, a.UTa_lo, a.ut_stride_a, a.Ia, p.Ia_pad, a.cmax_a, a.C,
+                                                    p.tiles_c, const_cast<unsigned char*>(a.At));
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
   const size_t smem = tc_smem_bytes(p);
   dim3 grid((unsigned)p.tiles_c, (unsigned)p.tiles_n, (unsigned)p.splits);
   if (a.nq <= 2)

@@ -58,6 +58,7 @@ struct TcArgs {
   int nkt_a, n_o, o_per_cta, nbuf;
   int Ia;                          // size of mode a
   int64_t ut_stride_a;             // row stride of UTa / UTa_lo (floats)
+  int skip_slice;                  // At already holds the current slices of U_a
 };
 
 int form_nsplit(int precision);
