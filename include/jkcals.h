@@ -186,6 +186,21 @@ jkcals_status jkcals_kernel_times(jkcals_t h, double* ms);
 jkcals_status jkcals_sweep_info(jkcals_t h, int* kernels_per_sweep, int* splits);
 
 /*
+ * jkcals_mode_plan -- how one mode's concurrent MTTKRP (Alg. 3 MTTKRP line) runs.
+ *  mode          0 <= mode < N, else JKCALS_ERR_ARG
+ *  kernel        receives 0 (FP64 on the CUDA cores), 1 (tensor cores, the Khatri-Rao
+ *                tile built in shared memory), 2 (exact-chain two-step form: one GEMM
+ *                against the sliced rows of mode fastest_mode per index of the remaining
+ *                modes, scaled by their factor entries in the epilogue)
+ *  tile_rows     NULL or receives the rows of the mode per CTA (N tile)
+ *  stages        NULL or receives the operand pipeline depth (0 for FP64)
+ *  fastest_mode  NULL or receives the other mode that runs fastest along the columns
+ *                of the operand layout (-1 for FP64)
+ */
+jkcals_status jkcals_mode_plan(jkcals_t h, int mode, int* kernel, int* tile_rows, int* stages,
+                               int* fastest_mode);
+
+/*
  * jkcals_run -- sweeps until every block is frozen or max_sweeps is reached.
  * With tol > 0 a block converges when |e_prev - e| / ||T_{-g}||^2 < tol
  * (stopping rule of Alg. 1/Alg. 3) and is frozen from then on.

@@ -168,6 +168,15 @@ class JKCALS:
         L.check(self._lib.jkcals_sweep_info(self._h, ct.byref(k), sp), "jkcals_sweep_info")
         return k.value, list(sp)
 
+    def mode_plan(self, mode: int):
+        """How mode `mode`'s MTTKRP runs: kernel ('fp64', 'tensor-core' or 'two-step'),
+        rows per CTA, pipeline stages and the fastest other mode of the operand layout."""
+        k, bn, st, fm = ct.c_int(), ct.c_int(), ct.c_int(), ct.c_int()
+        L.check(self._lib.jkcals_mode_plan(self._h, int(mode), ct.byref(k), ct.byref(bn), ct.byref(st),
+                                           ct.byref(fm)), "jkcals_mode_plan")
+        return {"kernel": ("fp64", "tensor-core", "two-step")[k.value], "tile_rows": bn.value,
+                "stages": st.value, "fastest_mode": fm.value}
+
     def run(self, max_sweeps: int, tol: float = 0.0):
         done = ct.c_int(0)
         fl = np.empty(self.K, dtype=np.float64)

@@ -1045,6 +1045,25 @@ jkcals_status jkcals_sweep_info(jkcals_t h, int* kernels_per_sweep, int* splits)
   return JKCALS_OK;
 }
 
+jkcals_status jkcals_mode_plan(jkcals_t h, int mode, int* kernel, int* tile_rows, int* stages, int* fastest_mode) {
+  JK_TRY(check_handle(h));
+  if (mode < 0 || mode >= h->N) return fail(JKCALS_ERR_ARG, "mode out of range");
+  if (kernel == nullptr) return fail(JKCALS_ERR_ARG, "kernel is NULL");
+  if (!h->tc) {
+    *kernel = 0;
+    if (tile_rows) *tile_rows = 64;
+    if (stages) *stages = 0;
+    if (fastest_mode) *fastest_mode = -1;
+    return JKCALS_OK;
+  }
+  const tc::TcPlan& p = h->tcplan[mode];
+  *kernel = p.tts ? 2 : 1;
+  if (tile_rows) *tile_rows = p.BN;
+  if (stages) *stages = p.stages;
+  if (fastest_mode) *fastest_mode = p.a_mode;
+  return JKCALS_OK;
+}
+
 jkcals_status jkcals_run(jkcals_t h, int max_sweeps, double tol, int* sweeps_done, double* final_loss) {
   JK_TRY(check_handle(h));
   if (max_sweeps < 0 || !(tol >= 0.0)) return fail(JKCALS_ERR_ARG, "bad max_sweeps or tol");

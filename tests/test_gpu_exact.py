@@ -120,3 +120,20 @@ def test_exact_gradient_matches_oracle():
     for n in range(4):
         err = np.linalg.norm(G[n] - G_ref[n]) / np.linalg.norm(G_ref[n])
         assert err <= 1e-8, (n, err)
+
+
+def test_mode_plan_reports_the_kernel_of_each_mode():
+    """The 300x100x50 workload runs mode 0 on the one-step kernel and the two narrow modes on
+    the two-step kernel against the sliced rows of mode 0; the FP64 form reports itself."""
+    _cuda()
+    w = W.make_config(2)
+    with api.from_workload(w, precision=PREC, device="cuda:0") as h:
+        p = [h.mode_plan(n) for n in range(3)]
+        with pytest.raises(api.JKError):
+            h.mode_plan(3)
+    assert p[0]["kernel"] == "tensor-core" and p[0]["stages"] >= 2
+    for n in (1, 2):
+        assert p[n] == {"kernel": "two-step", "tile_rows": 64, "stages": p[n]["stages"], "fastest_mode": 0}
+        assert p[n]["stages"] >= 2
+    with api.from_workload(W.make_config(1), device="cuda:0") as h:
+        assert h.mode_plan(0) == {"kernel": "fp64", "tile_rows": 64, "stages": 0, "fastest_mode": -1}
