@@ -51,6 +51,8 @@ def parse():
                         "on 400^3 delete-10 (R = --rank); 4: the batch of 64 uneven problems "
                         "(batched 3xTF32 + autotuner vs one launch per problem in FP64)")
     p.add_argument("--rank", type=int, default=10, help="configuration 3 rank (5, 10 or 20)")
+    p.add_argument("--rank-sweep", action="store_true",
+                   help="MTTKRP efficiency vs the number of components on 50x200x200 (Sec. 3.1 figure)")
     p.add_argument("--cpu-worker", action="store_true", help=argparse.SUPPRESS)
     p.add_argument("--seconds", type=float, default=15.0, help=argparse.SUPPRESS)
     return p.parse_args()
@@ -558,6 +560,66 @@ def cfg3_arm(args):
     print(json.dumps(out), flush=True)
 
 
+RANK_SWEEP_C = (1, 2, 5, 10, 20, 50, 100, 200, 500, 1000, 2000)
+RANK_SWEEP_FORMS = ("fp64", "tf32", "3xtf32", "bf16", "split_bf16", "exact_bf16")
+
+
+def rank_sweep_arm(args):
+    """Efficiency of the concurrent MTTKRP vs the number of columns C on a 50x200x200
+    tensor (the rank sweep of Sec. 3.1, here per precision form against the form's peak).
+    C columns are C/R models of R = min(C, 10) components with their own initial factors
+    and no left-out rows (plain concurrent ALS, Sec. 3.2).  Per C: the median MTTKRP time
+    of each mode (CUDA events around each launch inside the sweep graph), useful TFLOP/s =
+    2 C prod(I) / time, and the gain over C/10 separate rank-10 MTTKRPs.  The tensor
+    (16 MB) stays in L2 across sweeps."""
+    import numpy as np
+    import torch
+
+    from paper_2112_03985_gb300 import api, workloads as W
+
+    if not torch.cuda.is_available():
+        raise RuntimeError("bench.py needs a CUDA device (there is no CPU fallback)")
+    peaks, peak_src = load_peaks()
+    dims = (50, 200, 200)
+    E = float(np.prod(dims))
+    steps = min(args.steps, 20)
+    forms = {}
+    for prec in RANK_SWEEP_FORMS:
+        _, peak, note = roofline_peak(prec, peaks)
+        rows = []
+        for C in RANK_SWEEP_C:
+            R = min(C, 10)
+            K = C // R
+            w = W.make_workload("rank sweep", dims, 5, blocks=[np.zeros(0, dtype=np.int64)] * K, noise=0.01,
+                                seed=60, ranks=[R] * K)
+            rng = np.random.default_rng(61)
+            init = [rng.uniform(0.0, 1.0, size=(I, C)) for I in dims]
+            with api.JKCALS(w.T, 0, [R] * K, w.left_out, init, precision=prec, kernel_timing=True) as h:
+                h.als_sweep_async(args.warmup)
+                torch.cuda.synchronize()
+                times = []
+                for _ in range(steps):
+                    h.als_sweep_async(1)
+                    times.append(h.kernel_times())
+                torch.cuda.synchronize()
+            kt = np.median(np.array(times), axis=0)
+            tf = [2.0 * C * E / (t * 1e-3) / 1e12 for t in kt]
+            rows.append({"C": C, "mttkrp_us": [round(1e3 * float(t), 2) for t in kt],
+                         "tflops": [round(x, 3) for x in tf], "efficiency": [round(x / peak, 4) for x in tf]})
+        base = next(r for r in rows if r["C"] == 10)
+        for r in rows:
+            if r["C"] >= 10:
+                r["gain_vs_separate_rank10"] = [round((r["C"] / 10) * b / t, 2)
+                                                for b, t in zip(base["mttkrp_us"], r["mttkrp_us"])]
+        forms[prec] = {"peak_tflops": round(peak, 2), "peak": note, "rows": rows}
+    out = {"metric": "concurrent MTTKRP efficiency vs components (rank sweep)", "unit": "fraction of the form's peak",
+           "config": {"workload": "50x200x200 FP64 planted rank 5, 1% noise; C/R models of R = min(C, 10), "
+                                  "no left-out rows", "C": list(RANK_SWEEP_C), "peaks": peak_src,
+                      "sweeps_timed": steps, "warmup": args.warmup, "l2": "tensor resident (16 MB)"},
+           "forms": forms}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
     if args.cpu_worker:
@@ -565,6 +627,9 @@ def main():
         return
     if args.impl == "reference":
         reference_arm(args)
+        return
+    if args.rank_sweep:
+        rank_sweep_arm(args)
         return
     if args.config == 4:
         cfg4_arm(args)
