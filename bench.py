@@ -52,7 +52,7 @@ def parse():
                         "(batched 3xTF32 + autotuner vs one launch per problem in FP64)")
     p.add_argument("--rank", type=int, default=10, help="configuration 3 rank (5, 10 or 20)")
     p.add_argument("--rank-sweep", action="store_true",
-                   help="MTTKRP efficiency vs the number of components on 50x200x200 (Sec. 3.1 figure)")
+                   help="MTTKRP efficiency vs the number of components on 50x200x200 (Sec. 3.2 figure)")
     p.add_argument("--cpu-worker", action="store_true", help=argparse.SUPPRESS)
     p.add_argument("--seconds", type=float, default=15.0, help=argparse.SUPPRESS)
     return p.parse_args()
@@ -566,9 +566,9 @@ RANK_SWEEP_FORMS = ("fp64", "tf32", "3xtf32", "bf16", "split_bf16", "exact_bf16"
 
 def rank_sweep_arm(args):
     """Efficiency of the concurrent MTTKRP vs the number of columns C on a 50x200x200
-    tensor (the rank sweep of Sec. 3.1, here per precision form against the form's peak).
+    tensor (the rank sweep of Sec. 3.2, here per precision form against the form's peak).
     C columns are C/R models of R = min(C, 10) components with their own initial factors
-    and no left-out rows (plain concurrent ALS, Sec. 3.2).  Per C: the median MTTKRP time
+    and no left-out rows (plain concurrent ALS, Sec. 3.3).  Per C: the median MTTKRP time
     of each mode (CUDA events around each launch inside the sweep graph), useful TFLOP/s =
     2 C prod(I) / time, and the gain over C/10 separate rank-10 MTTKRPs.  The tensor
     (16 MB) stays in L2 across sweeps."""

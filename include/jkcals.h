@@ -186,6 +186,34 @@ jkcals_status jkcals_kernel_times(jkcals_t h, double* ms);
 jkcals_status jkcals_sweep_info(jkcals_t h, int* kernels_per_sweep, int* splits);
 
 /*
+ * jkcals_jackknife_se -- Alg. 2 post-processing on the device: every jackknife
+ * submodel (block with a non-empty left-out set, G of them, in block order) is
+ * adjusted to a reference model (Alg. 2 adjustment line: in every mode but the
+ * last, the entry of largest magnitude of each column made positive, the flip
+ * carried into the last mode; then the column permutation maximising
+ * sum_s prod_{n != sampled_mode} |cos(submodel column perm[s], reference column s)|,
+ * over all R! permutations for R <= 8 with ties to the lexicographically first,
+ * by the Hungarian method above), and the jackknife standard error
+ * S_n = sqrt((G-1)/G sum_g (U_n^g - mean_g U_n^g)^2) of every entry is formed
+ * (Alg. 2 std line) for the modes n != sampled_mode.  Uses the handle's current
+ * factors; synchronises.
+ *  ref_block    >= 0: the reference is that block's current factors (e.g. the full model
+ *               fitted in the same handle); < 0: ref gives it
+ *  ref          N pointers (host or device), row-major I_n x R FP64; ignored when ref_block >= 0
+ *  S            N pointers (host or device), row-major I_n x R FP64; S[sampled_mode] may be
+ *               NULL and is not written
+ *  perm         NULL or G x R int32 (host or device): reference column s <- submodel column perm[g][s]
+ *  aligned      NULL or N pointers (host or device), G x I_n x R FP64 (submodel-major):
+ *               the adjusted submodels
+ *  n_submodels  NULL or receives G
+ * Errors: JKCALS_ERR_ARG when fewer than two submodels, when the submodels (and the
+ * reference block) differ in rank, or for NULL arguments; JKCALS_ERR_OOM for the
+ * workspace (G + 2) x sum_n I_n x R doubles.
+ */
+jkcals_status jkcals_jackknife_se(jkcals_t h, int ref_block, const double* const* ref, double* const* S,
+                                  int32_t* perm, double* const* aligned, int* n_submodels);
+
+/*
  * jkcals_mode_plan -- how one mode's concurrent MTTKRP (Alg. 3 MTTKRP line) runs.
  *  mode          0 <= mode < N, else JKCALS_ERR_ARG
  *  kernel        receives 0 (FP64 on the CUDA cores), 1 (tensor cores, the Khatri-Rao

@@ -371,13 +371,15 @@ def sign_fix(U: Sequence[np.ndarray], last: int) -> List[np.ndarray]:
     return U
 
 
-def align_to_reference(U_sub: Sequence[np.ndarray], U_ref: Sequence[np.ndarray], n_hat: int):
+def align_to_reference(U_sub: Sequence[np.ndarray], U_ref: Sequence[np.ndarray], n_hat: int,
+                       return_perm: bool = False):
     """Permutation and scale adjustment of a submodel against the overall model
     (Alg. 2 adjustment line, method of Riu & Bro).  Reading: columns of modes
     other than the last are unit-norm (normalisation above) with the sign rule
     of ``sign_fix``; the permutation maximises sum_r prod_{n != n_hat}
     |cos(U_n^sub(:, r), U_n^ref(:, pi r))|, brute force for R <= 8, ties to the
-    lexicographically smallest permutation.  Returns the permuted factors."""
+    lexicographically smallest permutation.  Returns the permuted factors (and,
+    with ``return_perm``, perm: reference column s <- submodel column perm[s])."""
     N = len(U_sub)
     R = U_sub[0].shape[1]
     A = sign_fix(U_sub, N - 1)
@@ -402,7 +404,8 @@ def align_to_reference(U_sub: Sequence[np.ndarray], U_ref: Sequence[np.ndarray],
         perm = [0] * R
         for r_, s_ in zip(rows, cols):
             perm[s_] = r_
-    return [a[:, list(perm)] for a in A]
+    out = [a[:, list(perm)] for a in A]
+    return (out, list(perm)) if return_perm else out
 
 
 def jackknife_se(estimates: np.ndarray) -> np.ndarray:

@@ -88,6 +88,7 @@ class JKCALS:
         dims = (ct.c_int64 * self.N)(*self.dims)
         rk = (ct.c_int32 * self.K)(*self.ranks)
         ptr, idx = left_out_csr(left_out)
+        self._has_left_out = [bool(ptr[g + 1] > ptr[g]) for g in range(self.K)]
         self._keep = [T, ptr, idx, init]
         init_ptrs = (ct.c_void_p * self.N)(*[_ptr(u) for u in init])
         for n, u in enumerate(init):
@@ -198,6 +199,36 @@ class JKCALS:
     def set_factors(self, U):
         arr = (ct.c_void_p * self.N)(*[_ptr(u) for u in U])
         L.check(self._lib.jkcals_set_factors(self._h, arr), "jkcals_set_factors")
+
+    def jackknife_se(self, ref_block: Optional[int] = None, ref=None):
+        """Alg. 2 post-processing on the device: the submodels (blocks with left-out rows)
+        adjusted to a reference model, and the jackknife standard errors.  The reference is
+        block ``ref_block``'s factors or the factor list ``ref`` (I_n x R each).  Returns
+        (S, perm, aligned): S[n] is I_n x R (None for the sampled mode), perm is G x R
+        (reference column s <- submodel column perm[g, s]), aligned[n] is G x I_n x R."""
+        sub = [g for g in range(self.K) if self._has_left_out[g]]
+        if not sub:
+            raise ValueError("no submodel has left-out rows")
+        R = self.ranks[sub[0]]
+        G = len(sub)
+        S = [None if n == self.n_hat else np.empty((I, R)) for n, I in enumerate(self.dims)]
+        perm = np.empty((G, R), dtype=np.int32)
+        aligned = [np.empty((G, I, R)) for I in self.dims]
+        refs = None
+        if ref_block is None:
+            if ref is None:
+                raise ValueError("give ref_block or ref")
+            refs = [np.ascontiguousarray(r, dtype=np.float64) for r in ref]
+            refarr = (ct.c_void_p * self.N)(*[_ptr(r) for r in refs])
+        else:
+            refarr = None
+        Sarr = (ct.c_void_p * self.N)(*[None if s is None else _ptr(s) for s in S])
+        Aarr = (ct.c_void_p * self.N)(*[_ptr(a) for a in aligned])
+        got = ct.c_int(0)
+        L.check(self._lib.jkcals_jackknife_se(self._h, -1 if ref_block is None else int(ref_block), refarr, Sarr,
+                                              ct.c_void_p(_ptr(perm)), Aarr, ct.byref(got)), "jkcals_jackknife_se")
+        assert got.value == G
+        return S, perm, aligned
 
     def block_status(self):
         st = np.zeros(self.K, dtype=np.int32)

@@ -1064,6 +1064,90 @@ jkcals_status jkcals_mode_plan(jkcals_t h, int mode, int* kernel, int* tile_rows
   return JKCALS_OK;
 }
 
+jkcals_status jkcals_jackknife_se(jkcals_t h, int ref_block, const double* const* ref, double* const* S,
+                                  int32_t* perm, double* const* aligned, int* n_submodels) {
+  JK_TRY(check_handle(h));
+  const int N = h->N;
+  if (S == nullptr) return fail(JKCALS_ERR_ARG, "S is NULL");
+  for (int n = 0; n < N; ++n)
+    if (n != h->n_hat && S[n] == nullptr) return fail(JKCALS_ERR_ARG, "S[n] is NULL for a mode other than sampled_mode");
+  std::vector<int64_t> col_off;
+  for (int g = 0; g < h->K; ++g)
+    if (h->lo_ptr[g + 1] > h->lo_ptr[g]) col_off.push_back(h->off[g]);
+  const int G = (int)col_off.size();
+  if (G < 2) return fail(JKCALS_ERR_ARG, "the jackknife needs at least two submodels (blocks with left-out rows)");
+  int R = -1;
+  for (int g = 0; g < h->K; ++g) {
+    if (h->lo_ptr[g + 1] == h->lo_ptr[g]) continue;
+    if (R < 0) R = h->R[g];
+    if (h->R[g] != R) return fail(JKCALS_ERR_ARG, "the submodels differ in rank");
+  }
+  if (ref_block >= h->K) return fail(JKCALS_ERR_ARG, "ref_block out of range");
+  if (ref_block >= 0 && h->R[ref_block] != R) return fail(JKCALS_ERR_ARG, "ref_block's rank differs from the submodels'");
+  if (ref_block < 0) {
+    if (ref == nullptr) return fail(JKCALS_ERR_ARG, "ref is NULL and no ref_block given");
+    for (int n = 0; n < N; ++n)
+      if (ref[n] == nullptr) return fail(JKCALS_ERR_ARG, "ref[n] is NULL");
+  }
+  if (aligned != nullptr)
+    for (int n = 0; n < N; ++n)
+      if (aligned[n] == nullptr) return fail(JKCALS_ERR_ARG, "aligned[n] is NULL");
+
+  // workspace: submodel offsets, permutations, adjusted factors, S, external reference
+  size_t elems = 0;
+  for (int n = 0; n < N; ++n) elems += (size_t)h->dims[n] * R * ((size_t)G + 2);
+  const size_t perm_bytes = (sizeof(int32_t) * (size_t)G * R + 7) / 8 * 8;  // keeps the doubles 8-byte aligned
+  void* ws = nullptr;
+  JK_TRY(dalloc(h, &ws, sizeof(int64_t) * G + perm_bytes + sizeof(double) * elems));
+  struct Free {
+    jkcals_ctx* h;
+    void* p;
+    ~Free() { dfree(h, p); }
+  } free_ws{h, ws};
+  char* cur = static_cast<char*>(ws);
+  SeArgs a{};
+  a.N = N;
+  a.n_hat = h->n_hat;
+  a.R = R;
+  a.G = G;
+  a.C = h->C;
+  a.col_off = reinterpret_cast<const int64_t*>(cur);
+  JK_CUDA(h, cudaMemcpyAsync(cur, col_off.data(), sizeof(int64_t) * G, cudaMemcpyHostToDevice, h->stream));
+  cur += sizeof(int64_t) * G;
+  a.perm = reinterpret_cast<int32_t*>(cur);
+  cur += perm_bytes;
+  double* dcur = reinterpret_cast<double*>(cur);
+  for (int n = 0; n < N; ++n) {
+    a.dims[n] = h->dims[n];
+    a.U[n] = h->U[n];
+    const size_t E = (size_t)h->dims[n] * R;
+    a.aligned[n] = dcur;
+    dcur += E * G;
+    a.S[n] = dcur;
+    dcur += E;
+    if (ref_block >= 0) {
+      a.ref[n] = h->U[n] + h->off[ref_block];
+    } else {
+      JK_CUDA(h, cudaMemcpyAsync(dcur, ref[n], sizeof(double) * E, cudaMemcpyDefault, h->stream));
+      a.ref[n] = dcur;
+    }
+    dcur += E;
+  }
+  a.ref_ld = ref_block >= 0 ? h->C : R;
+  JK_CUDA(h, launch_jackknife_se(a, h->stream));
+  for (int n = 0; n < N; ++n) {
+    const size_t E = (size_t)h->dims[n] * R;
+    if (n != h->n_hat) JK_CUDA(h, cudaMemcpyAsync(S[n], a.S[n], sizeof(double) * E, cudaMemcpyDefault, h->stream));
+    if (aligned != nullptr)
+      JK_CUDA(h, cudaMemcpyAsync(aligned[n], a.aligned[n], sizeof(double) * E * G, cudaMemcpyDefault, h->stream));
+  }
+  if (perm != nullptr)
+    JK_CUDA(h, cudaMemcpyAsync(perm, a.perm, sizeof(int32_t) * G * R, cudaMemcpyDefault, h->stream));
+  JK_CUDA(h, cudaStreamSynchronize(h->stream));
+  if (n_submodels != nullptr) *n_submodels = G;
+  return JKCALS_OK;
+}
+
 jkcals_status jkcals_run(jkcals_t h, int max_sweeps, double tol, int* sweeps_done, double* final_loss) {
   JK_TRY(check_handle(h));
   if (max_sweeps < 0 || !(tol >= 0.0)) return fail(JKCALS_ERR_ARG, "bad max_sweeps or tol");

@@ -192,6 +192,21 @@ namespace jk {
 // ---- error plumbing (jk_capi.cu) --------------------------------------------
 void set_error(const std::string& msg);
 
+// ---- jackknife adjustment and standard errors (jk_se.cu) ---------------------
+struct SeArgs {
+  int N, n_hat, R, G;              // modes, sampled mode, common rank, submodels
+  int64_t dims[kMaxModes];
+  int64_t C;                       // columns of the multi-matrices
+  const double* U[kMaxModes];      // multi-matrices, I_k x C row-major
+  const int64_t* col_off;          // G: first column of submodel g
+  const double* ref[kMaxModes];    // reference factors, I_k x R, row stride ref_ld
+  int64_t ref_ld;
+  double* aligned[kMaxModes];      // G x I_k x R: adjusted submodels
+  int32_t* perm;                   // G x R: reference column s <- submodel column perm[s]
+  double* S[kMaxModes];            // I_k x R standard errors (k != n_hat)
+};
+cudaError_t launch_jackknife_se(const SeArgs& a, cudaStream_t s);
+
 // ---- create-time preparation (jk_prep.cu) -----------------------------------
 // T_(n) in Kolda column order from a dense C-order FP64 tensor on the device.
 cudaError_t launch_unfold_f64(const double* Tc, const int64_t* dims, int N, int n, double* out,

@@ -1,7 +1,7 @@
-"""GPU parity of plain concurrent ALS (Sec. 3.2, CALS): K models of one tensor, each with its
+"""GPU parity of plain concurrent ALS (Sec. 3.3, CALS): K models of one tensor, each with its
 own initial factors and rank, no left-out rows, advanced together through one MTTKRP per mode.
 Each model must follow its own CP-ALS run (Alg. 1) in the oracle.  Also the MTTKRP of the
-50x200x200 rank-sweep tensor (Sec. 3.1 figure) at the smallest column counts, every form.
+50x200x200 rank-sweep tensor (Sec. 3.2 figure) at the smallest column counts, every form.
 """
 import numpy as np
 import pytest

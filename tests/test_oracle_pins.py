@@ -252,6 +252,25 @@ def test_alignment_recovers_permutation_and_signs():
         np.testing.assert_allclose(al[k], ref_fixed[k], rtol=1e-14, atol=1e-15)
 
 
+@pytest.mark.parametrize("R", [8, 10, 20])
+def test_alignment_recovers_a_planted_permutation(R):
+    """Brute force (R = 8, 40320 permutations) and the assignment solver (R > 8) both
+    undo a planted column permutation with sign flips under small noise."""
+    rng = _rng(19 + R)
+    dims = (9, 30, 25)
+    ref = [rng.standard_normal((I, R)) for I in dims]
+    q = rng.permutation(R)
+    sub = [u[:, q] + 1e-3 * rng.standard_normal((u.shape[0], R)) for u in ref]
+    flip = rng.integers(0, 2, size=R) * 2 - 1
+    sub[1] = sub[1] * flip[None, :]
+    sub[2] = sub[2] * flip[None, :]
+    al, perm = O.align_to_reference(sub, ref, n_hat=0, return_perm=True)
+    assert [int(q[p]) for p in perm] == list(range(R))   # sub column perm[s] is ref column s
+    ref_fixed = O.sign_fix(ref, 2)
+    for k in (1, 2):
+        assert np.abs(al[k] - ref_fixed[k]).max() <= 1e-2
+
+
 def test_flop_counts_sec_4_2():
     """Sec. 4.2: JK-CALS / JK-ALS MTTKRP flops = I/(I-d) <= 2; the JK-ALS count
     equals 2R times the element count of the sliced tensors actually fitted."""
