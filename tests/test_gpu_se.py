@@ -54,6 +54,20 @@ def test_se_cfg1_against_the_full_model_block():
     _check(w.ranks, w.n_hat, w.left_out, U, ref, S, perm, aligned)
 
 
+def test_se_four_way_delete_groups_sampled_mode_two():
+    """Four-way tensor, sampled mode 2, delete-2 groups (the grouped jackknife), 20 sweeps;
+    the reference is the first submodel itself (its own permutation is the identity)."""
+    _cuda()
+    w = W.make_workload("t", (6, 5, 8, 7), 3, n_hat=2, blocks=W.group_blocks(8, 2), noise=0.01, seed=12)
+    with api.from_workload(w) as h:
+        h.als_sweep(20)
+        U = h.get_factors()
+        S, perm, aligned = h.jackknife_se(ref_block=0)
+    ref = [u[:, 0:3] for u in U]
+    np.testing.assert_array_equal(perm[0], np.arange(3, dtype=np.int32))
+    _check(w.ranks, w.n_hat, w.left_out, U, ref, S, perm, aligned)
+
+
 @pytest.mark.parametrize("R", [5, 8, 10, 20])
 def test_se_planted_permutations_external_reference(R):
     """Submodels planted as the reference with permuted, sign-flipped columns plus noise:
