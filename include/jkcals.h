@@ -229,6 +229,21 @@ jkcals_status jkcals_mode_plan(jkcals_t h, int mode, int* kernel, int* tile_rows
                                int* fastest_mode);
 
 /*
+ * jkcals_plan_query -- the plan jkcals_create would make, computed on the host alone
+ * (no device, no allocation, no handle): a tensor of N modes of sizes dims, K blocks of
+ * the given ranks, the options' precision and split setting, on a GPU of num_sms SMs.
+ *  kernel     N ints (host): per mode 0 (FP64), 1 (tensor cores, one-step), 2 (two-step)
+ *  tile_rows  NULL or N ints: rows of the mode per CTA
+ *  stages     NULL or N ints: operand pipeline depth (0 for FP64)
+ *  splits     NULL or N ints: split-K factor of the MTTKRP
+ * Errors: JKCALS_ERR_ARG for bad sizes or options; JKCALS_ERR_UNSUPPORTED where
+ * jkcals_create would refuse the shape (rank > 32, tiles or grids beyond the limits).
+ */
+jkcals_status jkcals_plan_query(int N, const int64_t* dims, int K, const int32_t* ranks,
+                                const jkcals_options* opt, int num_sms, int* kernel, int* tile_rows,
+                                int* stages, int* splits);
+
+/*
  * jkcals_run -- sweeps until every block is frozen or max_sweeps is reached.
  * With tol > 0 a block converges when |e_prev - e| / ||T_{-g}||^2 < tol
  * (stopping rule of Alg. 1/Alg. 3) and is frozen from then on.

@@ -39,6 +39,8 @@ SIGNATURES = {
     "jkcals_kernel_times": (ct.c_int, [P, ct.POINTER(ct.c_double)]),
     "jkcals_sweep_info": (ct.c_int, [P, ct.POINTER(ct.c_int), ct.POINTER(ct.c_int)]),
     "jkcals_jackknife_se": (ct.c_int, [P, ct.c_int, PP, PP, P, PP, ct.POINTER(ct.c_int)]),
+    "jkcals_plan_query": (ct.c_int, [ct.c_int, I64P, ct.c_int, I32P, ct.POINTER(Options), ct.c_int, I32P, I32P,
+                                     I32P, I32P]),
     "jkcals_mode_plan": (ct.c_int, [P, ct.c_int, ct.POINTER(ct.c_int), ct.POINTER(ct.c_int), ct.POINTER(ct.c_int),
                                     ct.POINTER(ct.c_int)]),
     "jkcals_run": (ct.c_int, [P, ct.c_int, ct.c_double, ct.POINTER(ct.c_int), P]),

@@ -338,6 +338,25 @@ def _loss_function():
     return _LOSS_FN
 
 
+def plan_query(dims: Sequence[int], ranks: Sequence[int], precision: str = "fp64", splits: int = 0,
+               num_sms: int = 152):
+    """The per-mode plan jkcals_create would make (host only, no device): kernel ('fp64',
+    'tensor-core' or 'two-step'), rows per CTA, pipeline stages and split-K factor."""
+    lib = L.load()
+    N, K = len(dims), len(ranks)
+    opt = L.Options()
+    lib.jkcals_default_options(ct.byref(opt))
+    opt.precision = L.PREC[precision]
+    opt.splits = int(splits)
+    d = (ct.c_int64 * N)(*[int(x) for x in dims])
+    rk = (ct.c_int32 * K)(*[int(r) for r in ranks])
+    out = [(ct.c_int32 * N)() for _ in range(4)]
+    L.check(lib.jkcals_plan_query(N, d, K, rk, ct.byref(opt), int(num_sms), *out), "jkcals_plan_query")
+    kinds = ("fp64", "tensor-core", "two-step")
+    return [{"kernel": kinds[out[0][n]], "tile_rows": out[1][n], "stages": out[2][n], "splits": out[3][n]}
+            for n in range(N)]
+
+
 def from_workload(w, precision: str = "fp64", device: Optional[str] = None, **kw) -> JKCALS:
     """Handle for a ``workloads.Workload`` (tensor in its dtype, init side by side)."""
     T = w.T.astype(np.float32) if w.dtype == "f32" else w.T

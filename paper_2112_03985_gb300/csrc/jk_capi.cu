@@ -1045,22 +1045,71 @@ jkcals_status jkcals_sweep_info(jkcals_t h, int* kernels_per_sweep, int* splits)
   return JKCALS_OK;
 }
 
-jkcals_status jkcals_mode_plan(jkcals_t h, int mode, int* kernel, int* tile_rows, int* stages, int* fastest_mode) {
-  JK_TRY(check_handle(h));
-  if (mode < 0 || mode >= h->N) return fail(JKCALS_ERR_ARG, "mode out of range");
-  if (kernel == nullptr) return fail(JKCALS_ERR_ARG, "kernel is NULL");
+// Mode n's plan as reported by jkcals_mode_plan / jkcals_plan_query.
+static void report_plan(const jkcals_ctx* h, int n, int* kernel, int* tile_rows, int* stages, int* fastest_mode,
+                        int* splits) {
   if (!h->tc) {
     *kernel = 0;
-    if (tile_rows) *tile_rows = 64;
+    if (tile_rows) *tile_rows = kMttkrpBM;
     if (stages) *stages = 0;
     if (fastest_mode) *fastest_mode = -1;
-    return JKCALS_OK;
+    if (splits) *splits = h->plan[n].splits;
+    return;
   }
-  const tc::TcPlan& p = h->tcplan[mode];
+  const tc::TcPlan& p = h->tcplan[n];
   *kernel = p.tts ? 2 : 1;
   if (tile_rows) *tile_rows = p.BN;
   if (stages) *stages = p.stages;
   if (fastest_mode) *fastest_mode = p.a_mode;
+  if (splits) *splits = p.splits;
+}
+
+jkcals_status jkcals_mode_plan(jkcals_t h, int mode, int* kernel, int* tile_rows, int* stages, int* fastest_mode) {
+  JK_TRY(check_handle(h));
+  if (mode < 0 || mode >= h->N) return fail(JKCALS_ERR_ARG, "mode out of range");
+  if (kernel == nullptr) return fail(JKCALS_ERR_ARG, "kernel is NULL");
+  report_plan(h, mode, kernel, tile_rows, stages, fastest_mode, nullptr);
+  return JKCALS_OK;
+}
+
+jkcals_status jkcals_plan_query(int N, const int64_t* dims, int K, const int32_t* ranks, const jkcals_options* opt,
+                                int num_sms, int* kernel, int* tile_rows, int* stages, int* splits) {
+  if (dims == nullptr || ranks == nullptr || kernel == nullptr) return fail(JKCALS_ERR_ARG, "NULL argument");
+  if (N < 2 || N > kMaxModes) return fail(JKCALS_ERR_ARG, "N must be in [2, 8]");
+  if (K < 1) return fail(JKCALS_ERR_ARG, "K must be >= 1");
+  if (num_sms < 1) return fail(JKCALS_ERR_ARG, "num_sms must be >= 1");
+  jkcals_options o;
+  jkcals_default_options(&o);
+  if (opt) o = *opt;
+  if (o.precision < JKCALS_FP64 || o.precision > JKCALS_EXACT_BF16) return fail(JKCALS_ERR_ARG, "bad precision");
+  if (o.splits < 0) return fail(JKCALS_ERR_ARG, "splits must be >= 0");
+  jkcals_ctx c;
+  c.N = N;
+  c.K = K;
+  c.opt = o;
+  c.tc = (o.precision != JKCALS_FP64);
+  c.num_sms = num_sms;
+  int64_t total = 1;
+  for (int k = 0; k < N; ++k) {
+    if (dims[k] < 1) return fail(JKCALS_ERR_ARG, "dims must be >= 1");
+    c.dims[k] = dims[k];
+    total *= dims[k];
+  }
+  for (int k = 0; k < N; ++k) c.J[k] = total / dims[k];
+  int64_t C = 0;
+  for (int g = 0; g < K; ++g) {
+    if (ranks[g] < 1) return fail(JKCALS_ERR_ARG, "ranks must be >= 1");
+    if (ranks[g] > kMaxRank) return fail(JKCALS_ERR_UNSUPPORTED, "ranks must be <= 32");
+    c.Rmax = std::max(c.Rmax, (int)ranks[g]);
+    C += ranks[g];
+  }
+  if (C > 2147483647LL) return fail(JKCALS_ERR_UNSUPPORTED, "too many columns");
+  c.C = (int)C;
+  make_plan(&c);
+  if (c.tc) JK_TRY(make_tc_plan(&c));
+  for (int n = 0; n < N; ++n)
+    report_plan(&c, n, &kernel[n], tile_rows ? &tile_rows[n] : nullptr, stages ? &stages[n] : nullptr, nullptr,
+                splits ? &splits[n] : nullptr);
   return JKCALS_OK;
 }
 

@@ -127,10 +127,15 @@ def test_mode_plan_reports_the_kernel_of_each_mode():
     the two-step kernel against the sliced rows of mode 0; the FP64 form reports itself."""
     _cuda()
     w = W.make_config(2)
+    import torch
     with api.from_workload(w, precision=PREC, device="cuda:0") as h:
         p = [h.mode_plan(n) for n in range(3)]
         with pytest.raises(api.JKError):
             h.mode_plan(3)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    q = api.plan_query(w.T.shape, w.ranks, PREC, num_sms=sms)   # the host-only planner agrees
+    assert [(a["kernel"], a["tile_rows"], a["stages"]) for a in p] == \
+        [(b["kernel"], b["tile_rows"], b["stages"]) for b in q]
     assert p[0]["kernel"] == "tensor-core" and p[0]["stages"] >= 2
     for n in (1, 2):
         assert p[n] == {"kernel": "two-step", "tile_rows": 64, "stages": p[n]["stages"], "fastest_mode": 0}
