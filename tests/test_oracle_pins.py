@@ -237,6 +237,17 @@ def test_jackknife_se_of_mean_is_s_over_sqrt_n():
     assert abs(O.jackknife_se(loo) - x.std(ddof=1) / np.sqrt(x.size)) <= 1e-14
 
 
+def test_grouped_jackknife_se_of_mean_is_se_of_group_means():
+    """Delete-d with G equal groups: leaving out group g moves the mean by -(ybar_g - xbar)/(G-1),
+    so the grouped jackknife SE of the mean equals std(group means, ddof=1) / sqrt(G)."""
+    G, d = 9, 4
+    x = _rng(21).standard_normal(G * d)
+    groups = x.reshape(G, d)
+    est = np.array([np.delete(x, np.arange(g * d, (g + 1) * d)).mean() for g in range(G)])
+    want = groups.mean(axis=1).std(ddof=1) / np.sqrt(G)
+    assert abs(O.jackknife_se(est) - want) <= 1e-14
+
+
 def test_alignment_recovers_permutation_and_signs():
     rng = _rng(18)
     ref = [rng.standard_normal((I, 4)) for I in (5, 6, 7)]
