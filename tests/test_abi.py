@@ -58,3 +58,27 @@ def test_options_struct_layout_matches_header():
     from paper_2112_03985_gb300 import _lib
     # int,int,int,int,int64,int[8] -> 4*4 + 8 + 32 = 56 bytes
     assert ctypes.sizeof(_lib.Options) == 56
+
+
+HANDLE_CALLS = ["jkcals_mttkrp", "jkcals_als_sweep", "jkcals_als_sweep_async", "jkcals_kernel_times",
+                "jkcals_sweep_info", "jkcals_mode_plan", "jkcals_jackknife_se", "jkcals_run", "jkcals_get_factors",
+                "jkcals_set_factors", "jkcals_get_block_status", "jkcals_grad", "jkcals_loss_history", "jkcals_sync"]
+
+
+@pytest.mark.parametrize("name", HANDLE_CALLS)
+def test_null_handle_is_an_argument_error(built_lib, name):
+    """Every call on a handle checks it first: a NULL handle returns JKCALS_ERR_ARG (no device
+    is touched) and leaves a message for jkcals_last_error."""
+    from paper_2112_03985_gb300 import _lib
+    lib = _lib.load()
+    _, argtypes = _lib.SIGNATURES[name]
+    args = []
+    for t in argtypes:
+        if t in (ctypes.c_int, ctypes.c_int32, ctypes.c_int64):
+            args.append(0)
+        elif t is ctypes.c_double:
+            args.append(0.0)
+        else:
+            args.append(None)
+    assert getattr(lib, name)(*args) == 1
+    assert b"NULL handle" in lib.jkcals_last_error()
