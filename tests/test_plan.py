@@ -7,7 +7,7 @@ import pytest
 from paper_2112_03985_gb300 import api
 
 FORMS = ("fp64", "tf32", "3xtf32", "bf16", "split_bf16", "exact_bf16")
-EXACT_BK = 64            # BF16 elements per 128-byte operand row
+EXACT_BK = 32            # BF16 elements per 64-byte operand row of the exact form
 EXACT_CHAIN_MAX = 1024   # columns of one exact chain
 
 
