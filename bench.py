@@ -95,6 +95,18 @@ def roofline_peak(precision, peaks):
     raise ValueError(precision)
 
 
+# Tensor-core products issued per useful multiply-add, per form (part products of the split forms).
+ISSUED_PER_USEFUL = {"fp64": 1, "tf32": 1, "bf16": 1, "3xtf32": 3, "split_bf16": 6, "exact_bf16": 10}
+
+
+def flops_views(achieved, precision, I_hat, d):
+    """The MTTKRP rate three ways (TFLOP/s): useful (2 C prod(I) per launch), the JK-ALS
+    equivalent (each submodel's own MTTKRP on its sliced tensor does (I - d)/I of that work,
+    Sec. 4.2), and the tensor-core products actually issued by the form."""
+    return {"useful": achieved, "jk_als_equivalent": achieved * (I_hat - d) / I_hat,
+            "issued": achieved * ISSUED_PER_USEFUL[precision]}
+
+
 # --------------------------------------------------------------------------- clocks
 
 class ClockSampler:
@@ -360,6 +372,8 @@ def gpu_arm(args):
             "flops_per_launch": flops_launch, "avg_launch_ms": mt.mean(),
             "peak_source": f"{peak_note} ({peak_src} MEASURED_PEAKS.json)" if bound != "alu" else peak_note,
             "mttkrp_share_of_step": float(mt.sum() / sum(kt_step_ms)),
+            "tflops_views": flops_views(achieved, args.precision, w.dims[w.n_hat],
+                                        max(len(D) for D in w.left_out)),
             "timing": "MTTKRP launches timed with CUDA events in a second pass of the same length "
                       "(event nodes around each launch); the headline pass has none"}
     losses_final = h.als_sweep(1)

@@ -46,3 +46,18 @@ def test_reference_arm_two_ranks_prints_once():
     assert len(lines) == 1, r.stdout
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["n_gpus"] == 2
+
+
+def test_flops_views_of_the_bench_workload():
+    """The three MTTKRP rates of the JSON line: the JK-ALS equivalent of the 300-sample
+    leave-one-out workload is 299/300 of the useful rate; the exact form issues ten tensor-core
+    products per useful one."""
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_2112_03985_gb300 import workloads as W
+    w = W.make_config(2)
+    v = bench.flops_views(60.0, "exact_bf16", w.dims[w.n_hat], max(len(D) for D in w.left_out))
+    assert v["useful"] == 60.0
+    assert abs(v["jk_als_equivalent"] - 60.0 * 299 / 300) < 1e-12
+    assert v["issued"] == 600.0
+    assert set(bench.ISSUED_PER_USEFUL) == {"fp64", "tf32", "3xtf32", "bf16", "split_bf16", "exact_bf16"}
