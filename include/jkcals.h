@@ -193,7 +193,7 @@ jkcals_status jkcals_sweep_info(jkcals_t h, int* kernels_per_sweep, int* splits)
  * carried into the last mode; then the column permutation maximising
  * sum_s prod_{n != sampled_mode} |cos(submodel column perm[s], reference column s)|,
  * over all R! permutations for R <= 8 with ties to the lexicographically first,
- * by the Hungarian method above), and the jackknife standard error
+ * by the Hungarian method for R > 8), and the jackknife standard error
  * S_n = sqrt((G-1)/G sum_g (U_n^g - mean_g U_n^g)^2) of every entry is formed
  * (Alg. 2 std line) for the modes n != sampled_mode.  Uses the handle's current
  * factors; synchronises.
