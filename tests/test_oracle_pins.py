@@ -230,6 +230,38 @@ def test_jk_als_blocks_match_separate_cp_als():
         np.testing.assert_allclose(r.normT2[g], np.sum(Tg * Tg))
 
 
+def test_noise_free_jackknife_submodels_agree_after_adjustment():
+    """An exact low-rank tensor stays exact when a slice is removed, so every leave-one-out
+    submodel recovers the planted model.  Started from column orders permuted per submodel,
+    the adjustment must undo each permutation; the jackknife SE then vanishes for the middle mode
+    and for the column directions of the last mode (its column scales and signs differ by
+    design: they carry the norms and sign flips of the sampled mode's columns, which lose a
+    different row per submodel)."""
+    rng = _rng(22)
+    dims, R = (9, 8, 7), 3
+    truth = [rng.standard_normal((I, R)) for I in dims]
+    T = O.cp_reconstruct(truth)
+    blocks = W.loo_blocks(dims[0])
+    perms, init = [], []
+    for _ in blocks:
+        q = rng.permutation(R)
+        perms.append(q)
+        init.append([u[:, q] + 1e-3 * rng.standard_normal(u.shape) for u in truth])
+    r = O.jk_als(T, 0, blocks, init, 300)
+    est = []
+    for g, D in enumerate(blocks):
+        Tg = O.slice_tensor(T, 0, D)
+        Ug = [O.remove_rows(r.factors[g][0], D), r.factors[g][1], r.factors[g][2]]
+        assert O.cp_loss_explicit(Tg, Ug) <= 1e-20 * np.sum(Tg * Tg)
+        A, p = O.align_to_reference(r.factors[g], truth, 0, return_perm=True)
+        assert [int(perms[g][j]) for j in p] == list(range(R))
+        last = A[2] / np.linalg.norm(A[2], axis=0)
+        last = last * np.sign(last[np.abs(last).argmax(axis=0), np.arange(R)])
+        est.append(np.concatenate([A[1].ravel(), last.ravel()]))
+    est = np.asarray(est)
+    assert O.jackknife_se(est).max() <= 1e-9 * np.abs(est).max()
+
+
 def test_jackknife_se_of_mean_is_s_over_sqrt_n():
     """Textbook identity: the jackknife SE of the sample mean equals s / sqrt(n)."""
     x = _rng(17).standard_normal(23)
