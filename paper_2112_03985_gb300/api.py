@@ -53,6 +53,13 @@ def multi_init(init_blocks: Sequence[Sequence[np.ndarray]]) -> List[np.ndarray]:
             for n in range(N)]
 
 
+def init_from_model(U: Sequence[np.ndarray], K: int) -> List[np.ndarray]:
+    """Initial multi-matrices of K jackknife submodels that all start from one fitted model U
+    (I_n x R per mode, Alg. 2 and Alg. 3 initialisation).  The rows each submodel leaves out
+    are zeroed by jkcals_create, so the model's factors are repeated unchanged."""
+    return multi_init([list(U)] * int(K))
+
+
 def _torch():
     import torch
     return torch

@@ -89,3 +89,4 @@ def test_plan_unsupported_shapes(dims, ranks, prec):
 def test_every_form_plans_every_small_shape():
     for prec, dims in itertools.product(FORMS, [(3, 3, 3), (1, 7, 2), (2, 2, 2, 2, 2)]):
         assert len(api.plan_query(dims, [1, 2], prec)) == len(dims)
+
