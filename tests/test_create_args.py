@@ -1,0 +1,80 @@
+"""jkcals_create's argument checks (no GPU): every invalid shape, block layout or option is
+rejected with its status and message before the device is touched."""
+import ctypes as ct
+
+import numpy as np
+import pytest
+
+from paper_2112_03985_gb300 import _lib as L
+
+ARG, UNSUPPORTED = 1, 7
+
+
+def _create(N=3, dims=(6, 5, 4), T=True, dtype=1, n_hat=0, ranks=(2, 2), ptr=(0, 1, 2), idx=(0, 3),
+            init=True, init_null=None, opt=None, out=True):
+    lib = L.load()
+    keep = []
+    d = np.asarray(dims, dtype=np.int64)
+    r = np.asarray(ranks, dtype=np.int32)
+    p = np.asarray(ptr, dtype=np.int64)
+    i = np.asarray(idx, dtype=np.int64) if idx is not None else None
+    Tbuf = np.zeros(4)
+    keep += [d, r, p, i, Tbuf]
+    inits = (ct.c_void_p * max(N, 1))()
+    for k in range(max(N, 1)):
+        a = np.zeros(4)
+        keep.append(a)
+        inits[k] = None if init_null == k else a.ctypes.data
+    o = L.Options()
+    lib.jkcals_default_options(ct.byref(o))
+    for key, val in (opt or {}).items():
+        setattr(o, key, val)
+    h = ct.c_void_p()
+    st = lib.jkcals_create(ct.byref(h) if out else None, N, d.ctypes.data_as(L.I64P),
+                           ct.c_void_p(Tbuf.ctypes.data) if T else None, dtype, n_hat, len(r),
+                           r.ctypes.data_as(L.I32P), p.ctypes.data_as(L.I64P),
+                           i.ctypes.data_as(L.I64P) if i is not None else None,
+                           inits if init else None, ct.byref(o), None)
+    assert not h.value
+    return st, lib.jkcals_last_error().decode()
+
+
+CASES = [
+    ("out NULL", dict(out=False), ARG, "out is NULL"),
+    ("one mode", dict(N=1, dims=(6,)), ARG, "N must be"),
+    ("nine modes", dict(N=9, dims=(2,) * 9), UNSUPPORTED, "N must be"),
+    ("T NULL", dict(T=False), ARG, "NULL argument"),
+    ("init NULL", dict(init=False), ARG, "NULL argument"),
+    ("bad dtype", dict(dtype=5), ARG, "T_dtype"),
+    ("empty mode", dict(dims=(6, 0, 4)), ARG, "dims must be >= 1"),
+    ("2^40 elements", dict(dims=(1 << 14, 1 << 14, 1 << 12)), UNSUPPORTED, "2^40"),
+    ("mode too long", dict(dims=(8388481, 1, 1)), UNSUPPORTED, "dims must be <="),
+    ("sampled mode", dict(n_hat=3), ARG, "sampled_mode"),
+    ("no blocks", dict(ranks=(), ptr=(0,), idx=None), ARG, "K must be"),
+    ("rank 0", dict(ranks=(2, 0)), ARG, "ranks must be >= 1"),
+    ("rank 33", dict(ranks=(2, 33)), UNSUPPORTED, "ranks must be <= 32"),
+    ("ptr start", dict(ptr=(1, 1, 2)), ARG, "left_out_ptr[0]"),
+    ("ptr order", dict(ptr=(0, 2, 1)), ARG, "non-decreasing"),
+    ("idx NULL", dict(idx=None), ARG, "left_out_idx is NULL"),
+    ("idx range", dict(idx=(0, 6)), ARG, "out of range"),
+    ("idx negative", dict(idx=(-1, 2)), ARG, "out of range"),
+    ("duplicate", dict(ptr=(0, 2, 2), idx=(3, 3)), ARG, "duplicate"),
+    ("leaves all out", dict(ptr=(0, 6, 6), idx=(0, 1, 2, 3, 4, 5)), ARG, "every sample"),
+    ("init[1] NULL", dict(init_null=1), ARG, "init[n] is NULL"),
+    ("precision", dict(opt={"precision": 9}), ARG, "precision"),
+    ("splits", dict(opt={"splits": -1}), ARG, "splits"),
+    ("update mode", dict(opt={"update_mode": 3}), ARG, "update_mode"),
+]
+
+
+@pytest.mark.parametrize("name,kw,status,msg", CASES, ids=[c[0] for c in CASES])
+def test_create_rejects(name, kw, status, msg):
+    st, err = _create(**kw)
+    assert st == status, (st, err)
+    assert msg in err, err
+
+
+def test_too_many_columns_is_unsupported():
+    K = 131071
+    st, err = _create(ranks=(32,) * K, ptr=(0,) * (K + 1), idx=None)
+    assert st == UNSUPPORTED and "sum of ranks" in err, err
