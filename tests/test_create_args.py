@@ -1,5 +1,6 @@
-"""jkcals_create's argument checks (no GPU): every invalid shape, block layout or option is
-rejected with its status and message before the device is touched."""
+"""Argument checks of the entry points that take no handle (no GPU): jkcals_create,
+jkcals_batch_create and jkcals_mttkrp_f64_noalloc reject every invalid shape, block layout or
+option with its status and message before the device is touched."""
 import ctypes as ct
 
 import numpy as np
@@ -78,3 +79,43 @@ def test_too_many_columns_is_unsupported():
     K = 131071
     st, err = _create(ranks=(32,) * K, ptr=(0,) * (K + 1), idx=None)
     assert st == UNSUPPORTED and "sum of ranks" in err, err
+
+
+def test_batch_create_needs_handles_and_sweeps():
+    lib = L.load()
+    b = ct.c_void_p()
+    hs = (ct.c_void_p * 1)(None)
+    assert lib.jkcals_batch_create(None, 1, hs, 10, None) == ARG
+    assert lib.jkcals_batch_create(ct.byref(b), 0, hs, 10, None) == ARG
+    assert lib.jkcals_batch_create(ct.byref(b), 1, None, 10, None) == ARG
+    assert lib.jkcals_batch_create(ct.byref(b), 1, hs, 0, None) == ARG
+    assert lib.jkcals_batch_create(ct.byref(b), 1, hs, 10, None) == ARG   # a NULL handle in the list
+    assert b.value is None
+
+
+NOALLOC = [
+    ("one mode", dict(N=1), ARG, "N must be"),
+    ("NULL dims", dict(dims=None), ARG, "NULL argument"),
+    ("mode", dict(mode=3), ARG, "mode out of range"),
+    ("no columns", dict(C=0), ARG, "C must be >= 1"),
+    ("too many columns", dict(C=65535 * 64 + 1), UNSUPPORTED, "C must be <="),
+    ("empty mode", dict(dims=(6, 0, 4)), ARG, "dims must be >= 1"),
+    ("2^40 elements", dict(dims=(1 << 14, 1 << 14, 1 << 12)), UNSUPPORTED, "2^40"),
+    ("scratch", dict(dims=(70000, 5, 4), C=32), UNSUPPORTED, "static scratch"),
+]
+
+
+@pytest.mark.parametrize("name,kw,status,msg", NOALLOC, ids=[c[0] for c in NOALLOC])
+def test_noalloc_rejects(name, kw, status, msg):
+    lib = L.load()
+    N = kw.get("N", 3)
+    dims = kw.get("dims", (6, 5, 4))
+    d = np.asarray(dims, dtype=np.int64) if dims is not None else None
+    buf = np.zeros(4)
+    U = (ct.c_void_p * 3)(buf.ctypes.data, buf.ctypes.data, buf.ctypes.data)
+    st = lib.jkcals_mttkrp_f64_noalloc(N, d.ctypes.data_as(L.I64P) if d is not None else None, kw.get("mode", 0),
+                                       ct.c_void_p(buf.ctypes.data), U, kw.get("C", 4),
+                                       ct.c_void_p(buf.ctypes.data), None)
+    err = lib.jkcals_last_error().decode()
+    assert st == status, (st, err)
+    assert msg in err, err
