@@ -234,7 +234,8 @@ class JKCALS:
         got = ct.c_int(0)
         L.check(self._lib.jkcals_jackknife_se(self._h, -1 if ref_block is None else int(ref_block), refarr, Sarr,
                                               ct.c_void_p(_ptr(perm)), Aarr, ct.byref(got)), "jkcals_jackknife_se")
-        assert got.value == G
+        if got.value != G:
+            raise RuntimeError(f"jkcals_jackknife_se counted {got.value} submodels, expected {G}")
         return S, perm, aligned
 
     def block_status(self):

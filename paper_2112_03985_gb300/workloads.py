@@ -112,7 +112,8 @@ def loo_blocks(I_hat: int, include_full: bool = False) -> List[np.ndarray]:
 
 def group_blocks(I_hat: int, d: int) -> List[np.ndarray]:
     """Delete-d with contiguous groups {d*g, ..., d*g+d-1} (Sec. 4.1, last remark)."""
-    assert I_hat % d == 0
+    if d < 1 or I_hat % d != 0:
+        raise ValueError(f"group size {d} must divide the {I_hat} samples")
     return [np.arange(g * d, (g + 1) * d, dtype=np.int64) for g in range(I_hat // d)]
 
 
