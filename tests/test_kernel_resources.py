@@ -1,6 +1,6 @@
 """Register budget of every kernel (no GPU): each translation unit is compiled for sm_103a with
 ptxas' resource report, and no kernel may spill registers to local memory.  One known
-exception is held to its present size: the fused update for ranks 9-16 of mixed-rank problems."""
+exception is held to its present size: the fused update's generic instantiation for ranks 9-16."""
 import os
 import re
 import shutil
