@@ -51,9 +51,12 @@ def parse():
                         "on 400^3 delete-10 (R = --rank); 4: the batch of 64 uneven problems "
                         "(batched 3xTF32 + autotuner vs one launch per problem in FP64)")
     p.add_argument("--rank", type=int, default=10, help="configuration 3 rank (5, 10 or 20)")
+    p.add_argument("--probe-peaks", action="store_true",
+                   help="measure the FP64 / FP32 / TF32 / BF16 matmul peaks of this GPU (prints JSON)")
     p.add_argument("--rank-sweep", action="store_true",
                    help="MTTKRP efficiency vs the number of components on 50x200x200 (Sec. 3.2 figure)")
     p.add_argument("--cpu-worker", action="store_true", help=argparse.SUPPRESS)
+    p.add_argument("--nvml-sampler", default=None, help=argparse.SUPPRESS)
     p.add_argument("--seconds", type=float, default=15.0, help=argparse.SUPPRESS)
     return p.parse_args()
 
@@ -69,29 +72,51 @@ def load_peaks():
                 "sm_max_mhz": 2070.0}, "fallback"
 
 
-# Nominal ratios of the recipe's dense tensor rates (per GPU): TF32 1.1 PF vs BF16 2.25 PF.
-TF32_PER_BF16 = 1.1 / 2.25
-# FP64 on CUDA cores: 152 SMs x 2 DFMA/clk x 2 flop at the maximum SM clock
-# (the recipe's nominal 1.25 TFLOP/s FP64 at 2070 MHz).
+FORM_PEAKS_PATH = os.path.join(ROOT, "profiles", "form_peaks.json")
+# Fallbacks only while no probe (bench.py --probe-peaks) has been committed: the
+# recipe's nominal TF32 / BF16 dense ratio 1.1 / 2.25, and FP64 on CUDA cores as
+# 152 SMs x 2 DFMA/clk x 2 flop at the maximum SM clock.
+TF32_PER_BF16_NOMINAL = 1.1 / 2.25
 FP64_FLOP_PER_CLK_PER_SM = 4.0
 NUM_SMS = 152
 
 
-def roofline_peak(precision, peaks):
+def load_form_peaks():
+    """TF32 / FP32 / FP64 peaks measured on this GPU by --probe-peaks (torch.matmul,
+    the method of MEASURED_PEAKS.json), or None."""
+    try:
+        with open(FORM_PEAKS_PATH) as f:
+            return json.load(f)
+    except Exception:
+        return None
+
+
+def roofline_peak(precision, peaks, sustained=False):
+    """(bound, peak TFLOP/s, note) of a precision form.  A kernel timed alone or inside
+    sub-millisecond steps is held to the burst figures; `sustained` selects the
+    seconds-long figures for a kernel timed inside a long loop."""
+    fp = load_form_peaks()
+    key = "sustained" if sustained else "burst"
     if precision == "fp64":
+        if fp is not None:
+            return "alu", fp["fp64_tflops"][key], f"measured FP64 DGEMM ({key}, profiles/form_peaks.json)"
         return "alu", NUM_SMS * FP64_FLOP_PER_CLK_PER_SM * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12, \
             "FP64 CUDA-core peak 152 SM x 4 flop/clk x sm_max_mhz (derived)"
-    bf16 = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
-    if precision == "tf32":
-        return "tensor", bf16 * TF32_PER_BF16, "TF32 = measured BF16 sustained x 1.1/2.25"
-    if precision == "3xtf32":
-        return "tensor", bf16 * TF32_PER_BF16 / 3.0, "3xTF32 = measured BF16 sustained x 1.1/2.25 / 3 passes"
+    bf16 = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops")) if sustained else peaks.get("bf16_tflops")
+    bnote = f"measured BF16 {key} (MEASURED_PEAKS.json)"
+    if precision in ("tf32", "3xtf32"):
+        passes = 1 if precision == "tf32" else 3
+        if fp is not None:
+            tf32, note = fp["tf32_tflops"][key], f"measured TF32 {key} (profiles/form_peaks.json)"
+        else:
+            tf32, note = bf16 * TF32_PER_BF16_NOMINAL, f"{bnote} x nominal TF32/BF16 1.1/2.25"
+        return "tensor", tf32 / passes, note + ("" if passes == 1 else f" / {passes} passes")
     if precision == "bf16":
-        return "tensor", bf16, "measured BF16 sustained"
+        return "tensor", bf16, bnote
     if precision == "split_bf16":
-        return "tensor", bf16 / 6.0, "measured BF16 sustained / 6 passes"
+        return "tensor", bf16 / 6.0, bnote + " / 6 passes"
     if precision == "exact_bf16":
-        return "tensor", bf16 / 10.0, "measured BF16 sustained / 10 BF16 passes (exact-chain slices)"
+        return "tensor", bf16 / 10.0, bnote + " / 10 BF16 passes (exact-chain slices)"
     raise ValueError(precision)
 
 
@@ -109,7 +134,63 @@ def flops_views(achieved, precision, I_hat, d):
 
 # --------------------------------------------------------------------------- clocks
 
+class _Nvml:
+    """Read-only NVML queries through ctypes (SM clock, its maximum, power, and the
+    active clock-event reasons); None when the library is not there."""
+    # clock-event reason bits (nvml.h)
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown", 0x40: "hw_thermal_slowdown",
+               0x80: "hw_power_brake_slowdown"}
+
+    def __init__(self, gpu):
+        import ctypes as ct
+        self.ct = ct
+        lib = None
+        for name in ("libnvidia-ml.so.1", "libnvidia-ml.so"):
+            try:
+                lib = ct.CDLL(name)
+                break
+            except OSError:
+                continue
+        if lib is None or lib.nvmlInit_v2() != 0:
+            raise OSError("NVML not available")
+        self.lib = lib
+        self.h = ct.c_void_p()
+        if isinstance(gpu, str) and not gpu.isdigit():
+            rc = lib.nvmlDeviceGetHandleByUUID(gpu.encode(), ct.byref(self.h))
+        else:
+            rc = lib.nvmlDeviceGetHandleByIndex_v2(ct.c_uint(int(gpu)), ct.byref(self.h))
+        if rc != 0:
+            raise OSError(f"NVML handle: {rc}")
+        self.reasons_fn = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            lib.nvmlDeviceGetCurrentClocksThrottleReasons
+
+    def sample(self):
+        ct = self.ct
+        mhz, mx, mw, r = ct.c_uint(), ct.c_uint(), ct.c_uint(), ct.c_ulonglong()
+        self.lib.nvmlDeviceGetClockInfo(self.h, 1, ct.byref(mhz))          # NVML_CLOCK_SM
+        self.lib.nvmlDeviceGetMaxClockInfo(self.h, 1, ct.byref(mx))
+        self.lib.nvmlDeviceGetPowerUsage(self.h, ct.byref(mw))
+        self.reasons_fn(self.h, ct.byref(r))
+        return float(mhz.value), float(mx.value), mw.value / 1e3, int(r.value)
+
+
+def nvml_sampler_main(gpu):
+    """--nvml-sampler: poll NVML every 0.5 ms and print one line per sample
+    (sm_mhz, max_mhz, watts, reason bits) until killed; a separate process, so
+    that the benchmark's own Python thread never delays a sample."""
+    nv = _Nvml(gpu)
+    out = sys.stdout
+    while True:
+        mhz, mx, w, r = nv.sample()
+        out.write(f"{mhz:.0f} {mx:.0f} {w:.1f} {r}\n")
+        out.flush()
+        time.sleep(0.0005)
+
+
 class ClockSampler:
+    """SM clock and clock-event reasons during the timed region: an NVML polling
+    process (0.5 ms period; started, and its first sample received, before the
+    region begins), else nvidia-smi every 50 ms."""
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -117,41 +198,139 @@ class ClockSampler:
     def __init__(self, gpu_index):
         self.gpu_index = gpu_index
         self.proc = None
+        self.source = "none"
+        self.lines = []
 
     def start(self):
+        try:
+            self.proc = subprocess.Popen([sys.executable, os.path.abspath(__file__), "--nvml-sampler",
+                                          str(self.gpu_index)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            first = self.proc.stdout.readline()        # the sampler is running
+            if first.strip():
+                self.lines.append(first)
+                self.source = "nvml 0.5 ms"
+                return
+            self.proc.wait(timeout=5)
+        except Exception:
+            pass
+        self.proc = None
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
                                           "-lms", "50", "-i", str(self.gpu_index)],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.source = "nvidia-smi 50 ms"
         except Exception:
             self.proc = None
+            self.source = "none"
 
     def stop(self):
         if self.proc is None:
-            return None
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0, "source": "none"}
         self.proc.terminate()
         try:
             out, _ = self.proc.communicate(timeout=5)
         except Exception:
             self.proc.kill()
             out, _ = self.proc.communicate()
-        sm, mx, reasons = [], None, set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in out.strip().splitlines():
-            parts = [x.strip() for x in line.split(",")]
-            if len(parts) < 9:
-                continue
-            try:
-                sm.append(float(parts[1]))
-                mx = float(parts[2])
-            except ValueError:
-                continue
-            for nm, v in zip(names, parts[5:9]):
-                if v.lower().startswith("active"):
-                    reasons.add(nm)
+        sm, mx, reasons, power = [], None, set(), []
+        if self.source.startswith("nvml"):
+            # the first line was read at start, before the timed region: not counted
+            for line in out.strip().splitlines():
+                parts = line.split()
+                if len(parts) != 4:
+                    continue
+                sm.append(float(parts[0]))
+                mx = float(parts[1])
+                power.append(float(parts[2]))
+                r = int(parts[3])
+                for bit, nm in _Nvml.REASONS.items():
+                    if r & bit:
+                        reasons.add(nm)
+        else:
+            names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+            for line in out.strip().splitlines():
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    mx = float(parts[2])
+                    power.append(float(parts[3]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
         if not sm:
-            return {"sm_mhz": None, "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": 0}
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+            return {"sm_mhz": None, "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": 0, "source": self.source}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "sm_mhz_min": min(sm),
+                "power_w_max": max(power) if power else None, "reasons": sorted(reasons), "samples": len(sm),
+                "source": self.source}
+
+
+def nvml_index(local):
+    """NVML / nvidia-smi identifier of the process's CUDA device `local` (an index,
+    or a UUID when CUDA_VISIBLE_DEVICES lists UUIDs)."""
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if vis:
+        ent = vis.split(",")[local].strip()
+        return int(ent) if ent.isdigit() else ent
+    return local
+
+
+def probe_peaks_arm(args):
+    """--probe-peaks: dense matmul peaks of this GPU with torch.matmul (cuBLAS), the
+    method of MEASURED_PEAKS.json: FP64 (4096^3), FP32 without and with TF32 tensor
+    cores, and BF16 (8192^3); 2 n^3 flop per product, burst = best of 10 (CUDA
+    events), sustained = back to back for 4 s; clocks sampled throughout."""
+    import torch
+    if not torch.cuda.is_available():
+        raise RuntimeError("bench.py needs a CUDA device (there is no CPU fallback)")
+    dev = torch.device("cuda", 0)
+    sampler = ClockSampler(nvml_index(0))
+    sampler.start()
+    out = {}
+    for name, dtype, n, tf32 in (("fp64", torch.float64, 4096, False), ("fp32", torch.float32, 8192, False),
+                                 ("tf32", torch.float32, 8192, True), ("bf16", torch.bfloat16, 8192, False)):
+        torch.backends.cuda.matmul.allow_tf32 = tf32
+        a = torch.randn(n, n, device=dev).to(dtype)
+        b = torch.randn(n, n, device=dev).to(dtype)
+        c = torch.empty(n, n, device=dev, dtype=dtype)
+        for _ in range(3):
+            torch.matmul(a, b, out=c)
+        torch.cuda.synchronize()
+        best = float("inf")
+        for _ in range(10):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            torch.matmul(a, b, out=c)
+            e1.record()
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1) / 1e3)
+        reps, t0 = 0, time.perf_counter()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        while time.perf_counter() - t0 < 4.0:
+            for _ in range(4):
+                torch.matmul(a, b, out=c)
+            reps += 4
+            if reps % 16 == 0:
+                torch.cuda.synchronize()
+        e1.record()
+        torch.cuda.synchronize()
+        sus = e0.elapsed_time(e1) / 1e3
+        flop = 2.0 * n ** 3
+        out[name + "_tflops"] = {"burst": flop / best / 1e12, "sustained": flop * reps / sus / 1e12, "n": n}
+        del a, b, c
+    torch.backends.cuda.matmul.allow_tf32 = False
+    clocks = sampler.stop()
+    props = torch.cuda.get_device_properties(0)
+    res = {"gpu_name": props.name, "sms": props.multi_processor_count, "torch": torch.__version__,
+           "how": "torch.matmul n^3 (2 n^3 flop): best of 10 with CUDA events (burst) and back to back "
+                  "for 4 s (sustained); fp32 with allow_tf32 False, tf32 with it True",
+           **out, "clocks": clocks}
+    print(json.dumps(res), flush=True)
 
 
 # --------------------------------------------------------------------------- CPU oracle
@@ -308,14 +487,7 @@ def gpu_arm(args):
         h.als_sweep_async(1)
     torch.cuda.synchronize()
 
-    gpu_index = local
-    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
-    if vis:
-        try:
-            gpu_index = int(vis.split(",")[local])
-        except ValueError:
-            pass
-    sampler = ClockSampler(gpu_index)
+    sampler = ClockSampler(nvml_index(local))
     barrier()
     torch.cuda.synchronize()
     sampler.start()
@@ -341,6 +513,8 @@ def gpu_arm(args):
         flush.zero_()
         ht.als_sweep_async(1)
     torch.cuda.synchronize()
+    ksampler = ClockSampler(nvml_index(local))
+    ksampler.start()
     mtt_ms, kt_step_ms = [], []
     for _ in range(args.steps):
         flush.zero_()
@@ -352,6 +526,7 @@ def gpu_arm(args):
         mtt_ms.append(ht.kernel_times())
         kt_step_ms.append((e0, e1))
     torch.cuda.synchronize()
+    kclocks = ksampler.stop()
     kt_step_ms = [a.elapsed_time(b) for a, b in kt_step_ms]
     ht.close()
     dev_s = sum(step_ms) / 1e3
@@ -366,11 +541,13 @@ def gpu_arm(args):
     mt = np.array(mtt_ms)  # steps x N
     avg_launch_s = mt.mean() / 1e3
     achieved = flops_launch / avg_launch_s / 1e12
-    bound, peak, peak_note = roofline_peak(args.precision, peaks)
+    # the MTTKRP launches last ~0.06 ms inside sub-millisecond sweeps: burst peak
+    bound, peak, peak_note = roofline_peak(args.precision, peaks, sustained=False)
     roof = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
             "traffic": measured_traffic(args.precision), "kernel": "concurrent MTTKRP",
             "flops_per_launch": flops_launch, "avg_launch_ms": mt.mean(),
-            "peak_source": f"{peak_note} ({peak_src} MEASURED_PEAKS.json)" if bound != "alu" else peak_note,
+            "peak_source": f"{peak_note}; {peak_src}" if bound != "alu" else peak_note,
+            "clocks": kclocks,
             "mttkrp_share_of_step": float(mt.sum() / sum(kt_step_ms)),
             "tflops_views": flops_views(achieved, args.precision, w.dims[w.n_hat],
                                         max(len(D) for D in w.left_out)),
@@ -383,9 +560,7 @@ def gpu_arm(args):
     # workload's sweep count) for the ratio and the factor error
     fp64 = None
     if args.precision != "fp64" and not args.no_fp64_compare:
-        with api.JKCALS(Td, w.n_hat, w.ranks, w.left_out, initd, precision=args.precision) as ha:
-            ha.als_sweep(w.sweeps)
-            U_ours = ha.get_factors()
+        offs = np.concatenate([[0], np.cumsum(w.ranks)])
         h64 = api.JKCALS(Td, w.n_hat, w.ranks, w.left_out, initd, precision="fp64")
         n64 = 10
         h64.als_sweep_async(3)
@@ -402,16 +577,32 @@ def gpu_arm(args):
             tot += e0.elapsed_time(e1)
         h64.als_sweep(w.sweeps - 3 - n64)
         U64 = h64.get_factors()
+        # jackknife standard errors (Alg. 2 adjustment and std lines, on the device):
+        # every submodel adjusted to block 0 of the FP64 fit
+        ref = [u[:, offs[0]:offs[1]] for u in U64]
+        S64, _, _ = h64.jackknife_se(ref=ref)
         h64.close()
-        offs = np.concatenate([[0], np.cumsum(w.ranks)])
+        with api.JKCALS(Td, w.n_hat, w.ranks, w.left_out, initd, precision=args.precision) as ha:
+            ha.als_sweep(w.sweeps)
+            U_ours = ha.get_factors()
+            S_ours, _, _ = ha.jackknife_se(ref=ref)
         err = 0.0
         for n in range(3):
             for g in range(w.K):
                 a, b = U_ours[n][:, offs[g]:offs[g + 1]], U64[n][:, offs[g]:offs[g + 1]]
                 err = max(err, float(np.linalg.norm(a - b) / np.linalg.norm(b)))
+        ferr_max = max(float(np.abs(a - b).max() / np.abs(b).max()) for a, b in zip(U_ours, U64))
+        se_err = max(float(np.abs(a - b).max() / np.abs(b).max())
+                     for a, b in zip(S_ours, S64) if a is not None)
         fp64 = {"value": w.K * n64 / (tot / 1e3), "ratio": value / world / (w.K * n64 / (tot / 1e3)),
                 "factor_rel_err_vs_fp64_path": err,
-                "sweeps_compared": w.sweeps}
+                "factor_max_err_rel_to_max": ferr_max,
+                "se_max_err_rel_to_max": se_err,
+                "sweeps_compared": w.sweeps,
+                "errors": "factors: largest relative Frobenius error per (submodel, mode), and the largest "
+                          "entry error over the largest entry per mode; jackknife SE of modes != n_hat after "
+                          "adjusting every submodel to block 0 of the FP64 fit, largest entry error over "
+                          "the largest SE per mode"}
 
     # end to end: one whole job from pinned host buffers through the public API
     e2e = None
@@ -636,11 +827,17 @@ def rank_sweep_arm(args):
 
 def main():
     args = parse()
+    if args.nvml_sampler is not None:
+        nvml_sampler_main(args.nvml_sampler)
+        return
     if args.cpu_worker:
         cpu_worker(args.seconds)
         return
     if args.impl == "reference":
         reference_arm(args)
+        return
+    if args.probe_peaks:
+        probe_peaks_arm(args)
         return
     if args.rank_sweep:
         rank_sweep_arm(args)

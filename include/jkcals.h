@@ -71,8 +71,11 @@ typedef enum {
                              the split-K partials summed into FP64.  Modes of <= 128 rows
                              whose largest other mode has >= 128 run a two-step variant
                              (GEMMs against the sliced rows of that mode, scaled by the
-                             remaining modes' entries).  About FP64-level MTTKRP accuracy
-                             on the tensor cores (10 BF16 MMA passes). */
+                             remaining modes' entries).  Measured accuracy: MTTKRP
+                             within ~2e-9 relative of FP64 (tested at 1e-8 element by
+                             element), factors within ~4e-8 of the FP64 path after 100
+                             sweeps of the 300x100x50 workload (tested at 1e-6); not the
+                             FP64 form's 1e-12.  10 BF16 MMA passes per product. */
 } jkcals_prec;
 
 typedef enum { JKCALS_DTYPE_F32 = 0, JKCALS_DTYPE_F64 = 1 } jkcals_dtype;
@@ -347,8 +350,12 @@ jkcals_status jkcals_sync(jkcals_t h);
  * shares the array and overwrites, before reading, every element it uses, so
  * the previous call's leftovers never matter; but calls whose work overlaps on
  * the GPU (other streams, other host threads) race on the array and give wrong
- * results: serialise them, e.g. on one stream.  Host pointers for Tn, U[k] or
- * M_out are rejected with JKCALS_ERR_ARG.  Returns after enqueueing (no sync).
+ * results: serialise them, e.g. on one stream.  The looked-up address is kept
+ * for the life of the process: after cudaDeviceReset (or any teardown of the
+ * device's primary context) the entry point must not be called again in that
+ * process.  Tn, U[k] and M_out must be device (or managed) memory of the
+ * current device; host pointers and pointers into another GPU's memory are
+ * rejected with JKCALS_ERR_ARG.  Returns after enqueueing (no sync).
  */
 jkcals_status jkcals_mttkrp_f64_noalloc(int N, const int64_t* dims, int mode, const double* Tn,
                                         const double* const* U, int C, double* M_out, void* stream);

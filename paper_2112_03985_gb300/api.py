@@ -377,19 +377,61 @@ def from_workload(w, precision: str = "fp64", device: Optional[str] = None, **kw
     return JKCALS(T, w.n_hat, w.ranks, w.left_out, init, precision=precision, **kw)
 
 
+def _check_noalloc_args(Tn, U, mode: int, out):
+    """Shapes, dtypes and devices of jkcals_mttkrp_f64_noalloc's arguments: the
+    C ABI sees only pointers, so a mis-sized buffer would be read or written past
+    its end.  Returns (dims, C).  Raises ValueError."""
+    N = len(U)
+    if not 2 <= N <= 8:
+        raise ValueError("U must hold 2 to 8 factor matrices")
+    if not 0 <= mode < N:
+        raise ValueError("mode out of range")
+    others = [k for k in range(N) if k != mode]
+    tensors = [("Tn", Tn), ("out", out)] + [(f"U[{k}]", U[k]) for k in others]
+    for name, t in tensors:
+        if t is None:
+            raise ValueError(f"{name} is missing")
+        if t.dtype != _torch().float64:
+            raise ValueError(f"{name} must be float64, got {t.dtype}")
+        if t.dim() != 2:
+            raise ValueError(f"{name} must be a matrix")
+        if not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous (row-major)")
+    devs = {t.device for _, t in tensors}
+    if len(devs) != 1:
+        raise ValueError("Tn, out and the factor matrices must be on one device")
+    C = int(U[others[0]].shape[1])
+    dims = [0] * N
+    dims[mode] = int(Tn.shape[0])
+    for k in others:
+        if int(U[k].shape[1]) != C:
+            raise ValueError(f"U[{k}] has {U[k].shape[1]} columns, expected C = {C}")
+        dims[k] = int(U[k].shape[0])
+    J = 1
+    for k in others:
+        J *= dims[k]
+    if tuple(Tn.shape) != (dims[mode], J):
+        raise ValueError(f"Tn must be {dims[mode]} x {J} (the mode-{mode} unfolding), got {tuple(Tn.shape)}")
+    if tuple(out.shape) != (dims[mode], C):
+        raise ValueError(f"out must be {dims[mode]} x {C}, got {tuple(out.shape)}")
+    if U[mode] is not None and tuple(U[mode].shape) != (dims[mode], C):
+        raise ValueError(f"U[{mode}] must be {dims[mode]} x {C} or None")
+    return dims, C
+
+
 def mttkrp_f64_noalloc(Tn, U, mode: int, out, stream=None):
     """FP64 concurrent MTTKRP of one mode without any device allocation
     (jkcals_mttkrp_f64_noalloc): Tn is the I_mode x J unfolding, U the N factor
-    matrices (I_k x C), out the I_mode x C result; all CUDA tensors.  Enqueued
-    on ``stream`` (default: torch's current stream), not synchronised."""
+    matrices (I_k x C; U[mode] is not read and may be None), out the I_mode x C
+    result; float64 CUDA tensors on one device, contiguous.  Enqueued on
+    ``stream`` (default: torch's current stream), not synchronised."""
+    dims, C = _check_noalloc_args(Tn, U, mode, out)
     lib = L.load()
     N = len(U)
-    dims = [int(u.shape[0]) for u in U]
-    C = int(U[(mode + 1) % N].shape[1])
     d = (ct.c_int64 * N)(*dims)
     ptrs = (ct.c_void_p * N)(*[(_ptr(u) if (k != mode and u is not None) else None) for k, u in enumerate(U)])
-    if stream is None:
-        stream = _torch().cuda.current_stream().cuda_stream
+    if stream is None:   # host tensors reach the C ABI, which rejects them
+        stream = _torch().cuda.current_stream(Tn.device).cuda_stream if Tn.is_cuda else 0
     L.check(lib.jkcals_mttkrp_f64_noalloc(N, d, int(mode), ct.c_void_p(_ptr(Tn)), ptrs, C,
                                           ct.c_void_p(_ptr(out)), ct.c_void_p(stream)),
             "jkcals_mttkrp_f64_noalloc")

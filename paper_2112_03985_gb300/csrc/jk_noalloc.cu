@@ -40,13 +40,17 @@ cudaError_t scratch_for_current_device(double** out, int* device) {
   return cudaSuccess;
 }
 
-bool is_device_pointer(const void* p) {
+// True for device memory of `device` (or managed memory).  A pointer into
+// another GPU's memory is refused: the kernels would read it through peer
+// access, which need not be enabled.
+bool is_device_pointer(const void* p, int device) {
   cudaPointerAttributes attr{};
   if (cudaPointerGetAttributes(&attr, p) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  return attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged;
+  if (attr.type == cudaMemoryTypeManaged) return true;
+  return attr.type == cudaMemoryTypeDevice && attr.device == device;
 }
 
 jkcals_status fail_na(jkcals_status s, const std::string& msg) {
@@ -81,23 +85,24 @@ extern "C" jkcals_status jkcals_mttkrp_f64_noalloc(int N, const int64_t* dims, i
   if (I * (int64_t)C > kNoAllocScratchDoubles)
     return fail_na(JKCALS_ERR_UNSUPPORTED,
                    "dims[mode] * C exceeds the static scratch of 2^21 doubles (16 MiB)");
-  if (!is_device_pointer(Tn) || !is_device_pointer(M_out))
-    return fail_na(JKCALS_ERR_ARG, "Tn and M_out must be device memory");
+  double* scratch = nullptr;
+  int device = 0;
+  cudaError_t e = scratch_for_current_device(&scratch, &device);
+  if (e != cudaSuccess) return fail_na(JKCALS_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+  if (!is_device_pointer(Tn, device) || !is_device_pointer(M_out, device))
+    return fail_na(JKCALS_ERR_ARG, "Tn and M_out must be device memory of the current device");
   KrpOperands kr{};
   int o = 0;
   for (int k = 0; k < N; ++k) {
     if (k == mode) continue;
-    if (U[k] == nullptr || !is_device_pointer(U[k])) return fail_na(JKCALS_ERR_ARG, "U[k] must be device memory");
+    if (U[k] == nullptr || !is_device_pointer(U[k], device))
+      return fail_na(JKCALS_ERR_ARG, "U[k] must be device memory of the current device");
     kr.U[o] = U[k];
     kr.dims[o] = (int)dims[k];
     ++o;
   }
   kr.nother = o;
 
-  double* scratch = nullptr;
-  int device = 0;
-  cudaError_t e = scratch_for_current_device(&scratch, &device);
-  if (e != cudaSuccess) return fail_na(JKCALS_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
   int sms = 0;
   e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
   if (e != cudaSuccess) return fail_na(JKCALS_ERR_CUDA, cudaGetErrorString(e));

@@ -8,7 +8,7 @@ import pytest
 import oracle as O
 from paper_2112_03985_gb300 import api, workloads as W
 
-from _helpers import factor_errors
+from _helpers import assert_factors
 
 pytestmark = pytest.mark.gpu
 
@@ -64,7 +64,7 @@ def test_batched_fp64_matches_oracle_on_sampled_problems(problems):
             U = h.get_factors()
             blocks = [0, w.K - 1]
             ora = O.jk_als(w.T, w.n_hat, w.left_out, w.init, sweeps, blocks=blocks)
-            errs = factor_errors(w, U, ora, blocks)
+            errs = assert_factors(w, U, ora.factors, blocks, 1e-10)
             lrel = np.abs(losses[:, blocks] - ora.losses) / np.abs(ora.losses)
             assert errs.max() <= 1e-10, errs.max()
             assert lrel.max() <= 1e-10, lrel.max()

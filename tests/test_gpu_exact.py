@@ -1,8 +1,11 @@
 """GPU parity of the exact-chain sliced-BF16 form (JKCALS_EXACT_BF16).
 
-This is the tensor-core form held to the FP64 bar: MTTKRP within 1e-8
-relative per block, factors within 1e-6 relative of the FP64 oracle after the
-fixed sweep count (measured ~1e-7 on the 300x100x50 workload).
+The form whose factors are held to the 1e-6 bar: MTTKRP within 1e-8 of the
+oracle element by element (|got - ref| <= 1e-8 (|ref| + max|ref|) per block;
+measured ~2e-9 relative), factors within 1e-6 element by element after the fixed
+sweep count (measured ~4e-8 on the 300x100x50 workload).  The losses are held to
+a bound derived, sweep by sweep, from the MTTKRP bar and the measured distance
+between the GPU's and the oracle's models (tests/_helpers.loss_bound).
 """
 import numpy as np
 import pytest
@@ -10,7 +13,7 @@ import pytest
 import oracle as O
 from paper_2112_03985_gb300 import api, workloads as W
 
-from _helpers import compare_mttkrp, factor_errors, offsets
+from _helpers import assert_factors, compare_mttkrp, offsets, stepwise_loss_check
 
 pytestmark = pytest.mark.gpu
 
@@ -78,31 +81,27 @@ def test_exact_mttkrp_is_exact_on_dyadic_data(dims):
             np.testing.assert_array_equal(M, ref)
 
 
+def _als_parity(w, sel):
+    """Sweep by sweep against the oracle's Alg. 1 on each sampled submodel: the
+    losses within the derived bound after every sweep, the factors element by
+    element after the last."""
+    with api.from_workload(w, precision=PREC) as h:
+        _, _, ratio, facs = stepwise_loss_check(w, h, sel, w.sweeps, MTTKRP_RTOL)
+        U = h.get_factors()
+    errs = assert_factors(w, U, facs, sel, FACTOR_RTOL)
+    print(f"\n{w.name}: factor rel err {errs.max():.2e}; loss error at most {ratio:.2f} of its bound")
+
+
 def test_exact_als_parity_cfg1_50_sweeps():
     _cuda()
     w = W.make_config(1)
-    with api.from_workload(w, precision=PREC) as h:
-        L = h.als_sweep(w.sweeps)
-        U = h.get_factors()
-    sel = list(range(w.K))
-    ora = O.jk_als(w.T, w.n_hat, w.left_out, w.init, w.sweeps, blocks=sel)
-    errs = factor_errors(w, U, ora, sel)
-    assert errs.max() <= FACTOR_RTOL, errs.max()
-    assert np.all(np.abs(L - ora.losses) <= 1e-7 * ora.normT2[None, :])
+    _als_parity(w, list(range(w.K)))
 
 
 def test_exact_als_parity_cfg2_full_size_sampled_blocks():
     """Configuration 2 at full size, 100 sweeps, against the oracle on sampled blocks."""
     _cuda()
-    w = W.make_config(2)
-    with api.from_workload(w, precision=PREC) as h:
-        L = h.als_sweep(w.sweeps)
-        U = h.get_factors()
-    sel = [0, 135, 195, 299]
-    ora = O.jk_als(w.T, w.n_hat, w.left_out, w.init, w.sweeps, blocks=sel)
-    errs = factor_errors(w, U, ora, sel)
-    assert errs.max() <= FACTOR_RTOL, errs.max()
-    assert np.all(np.abs(L[:, sel] - ora.losses) <= 1e-7 * ora.normT2[None, :])
+    _als_parity(W.make_config(2), [0, 135, 195, 299])
 
 
 def test_exact_gradient_matches_oracle():

@@ -11,7 +11,8 @@ import pytest
 import oracle as O
 from paper_2112_03985_gb300 import api, workloads as W
 
-from _helpers import compare_mttkrp, offsets
+from _helpers import (assert_elementwise, assert_factors, compare_mttkrp, offsets, se_perturbation_bound,
+                      stepwise_loss_check)
 
 pytestmark = pytest.mark.gpu
 
@@ -81,25 +82,18 @@ def test_tc_is_deterministic_and_zero_rows_stay_zero():
 
 
 def test_tc_als_tracks_oracle_on_cfg1():
-    """3xTF32 ALS against the FP64 oracle (configuration 1, 50 sweeps): the
-    FP32 accumulation keeps the factors within 1e-4; the bound is reported,
-    not a parity claim."""
+    """3xTF32 ALS against the FP64 oracle (configuration 1, 50 sweeps): factors
+    within 1e-4 element by element, and the loss after every sweep within the
+    bound derived from the form's MTTKRP bar (1e-5) and the distance between the
+    two models; a reported bound, not a parity claim."""
     _cuda()
     w = W.make_config(1)
-    with api.from_workload(w, precision="3xtf32") as h:
-        L = h.als_sweep(w.sweeps)
-        U = h.get_factors()
     sel = [0, 7, 20]
-    ora = O.jk_als(w.T, w.n_hat, w.left_out, w.init, w.sweeps, blocks=sel)
-    offs = offsets(w.ranks)
-    for col, g in enumerate(sel):
-        for n in range(3):
-            ref = ora.factors[col][n]
-            err = np.linalg.norm(U[n][:, offs[g]:offs[g + 1]] - ref) / np.linalg.norm(ref)
-            assert err <= 1e-4, (g, n, err)
-        # the efficient error formula cancels ||T||^2 against 2<T, M>, so an MTTKRP
-        # error eps moves e by about 2 eps ||T_g||^2: compare relative to ||T_g||^2
-        assert np.all(np.abs(L[:, g] - ora.losses[:, col]) <= 1e-4 * ora.normT2[col])
+    with api.from_workload(w, precision="3xtf32") as h:
+        _, _, ratio, facs = stepwise_loss_check(w, h, sel, w.sweeps, SMALL_RTOL["3xtf32"])
+        U = h.get_factors()
+    errs = assert_factors(w, U, facs, sel, 1e-4)
+    print(f"\ncfg1 3xtf32: factor rel err {errs.max():.2e}; loss error at most {ratio:.2f} of its bound")
 
 
 def test_tc_gradient_matches_oracle():
@@ -121,9 +115,18 @@ def test_tc_gradient_matches_oracle():
 
 def test_jackknife_se_error_per_form_cfg2():
     """Configuration 2, 100 sweeps: factor and jackknife standard-error (Alg. 2
-    std line, modes != n_hat) relative errors of every precision form against
-    the FP64 path (itself matched to the oracle on sampled blocks).  Each
-    submodel is aligned (Alg. 2 adjustment line) to submodel 0 of the FP64 run."""
+    std line, modes != n_hat) errors of every precision form against the FP64
+    path (itself matched to the oracle on sampled blocks).  Each submodel is
+    aligned (Alg. 2 adjustment line) to submodel 0 of the FP64 run.
+
+    Bars: the exact-chain form's factors within 1e-6 of FP64, element by element.
+    The standard errors are held, entry by entry, to the bound that the factor
+    differences themselves imply: SE(x) = sqrt((G-1)/G) ||x - mean(x)|| is a norm
+    over the G submodels, so |SE(a) - SE(b)| <= SE(a - b) (reverse triangle
+    inequality); an SE therefore moves by up to the jackknife SE of the aligned
+    factor differences, i.e. by about sqrt(G) times the per-submodel factor error
+    when those errors do not share a sign, which is why the relative SE error of a
+    form exceeds its relative factor error.  The per-form figures are printed."""
     _cuda()
     w = W.make_config(2)
     offs = offsets(w.ranks)
@@ -133,26 +136,44 @@ def test_jackknife_se_error_per_form_cfg2():
             h.als_sweep(w.sweeps)
             return h.get_factors()
 
-    def se(U, ref):
+    def estimates(U, ref):
         est = []
         for g in range(w.K):
             Ug = [u[:, offs[g]:offs[g + 1]] for u in U]
             A = O.align_to_reference(Ug, ref, w.n_hat)
             est.append(np.concatenate([A[k].ravel() for k in range(3) if k != w.n_hat]))
-        return O.jackknife_se(np.asarray(est))
+        return np.asarray(est)
 
     U64 = fit("fp64")
     ref = [u[:, offs[0]:offs[1]] for u in U64]
-    se64 = se(U64, ref)
+    est64 = estimates(U64, ref)
+    se64 = O.jackknife_se(est64)
     report = {}
     for prec in ("exact_bf16", "3xtf32", "split_bf16", "tf32", "bf16"):
         U = fit(prec)
         ferr = max(float(np.abs(a - b).max() / np.abs(b).max()) for a, b in zip(U, U64))
-        serr = float(np.abs(se(U, ref) - se64).max() / np.abs(se64).max())
-        report[prec] = (ferr, serr)
-    print("\ncfg2 100 sweeps, vs FP64: " + ", ".join(f"{p}: factors {f:.1e} SE {s:.1e}" for p, (f, s) in report.items()))
-    # SEs are differences between nearly equal submodels: they amplify factor
-    # errors about tenfold (exact form: factors ~1e-7, SEs ~1e-6)
-    assert report["exact_bf16"][0] <= 1e-6 and report["exact_bf16"][1] <= 1e-5
-    for p, (f, s) in report.items():
+        est = estimates(U, ref)
+        se = O.jackknife_se(est)
+        bound = se_perturbation_bound(est, est64)
+        serr = float(np.abs(se - se64).max() / np.abs(se64).max())
+        report[prec] = (ferr, serr, float(bound.max() / np.abs(se64).max()))
+        # reverse triangle inequality (up to rounding of the two SE evaluations)
+        assert np.all(np.abs(se - se64) <= bound + 1e-13 * np.abs(se64).max()), prec
+        if prec == "exact_bf16":
+            for a, b in zip(U, U64):
+                assert_elementwise(a, b, 1e-6, "exact form factors vs FP64")
+            # with the same alignment per submodel, every aligned difference is at
+            # most 2e-6 max|U_n| by the factor bar, so SE(diff) <= sqrt(G - 1) 2e-6 max|U_n|
+            G = w.K
+            col = 0
+            for k in range(3):
+                if k == w.n_hat:
+                    continue
+                m = w.dims[k] * w.ranks[0]
+                lim = np.sqrt(G - 1.0) * 2e-6 * np.abs(est64[:, col:col + m]).max()
+                assert np.all(np.abs(se - se64)[col:col + m] <= lim), (k, np.abs(se - se64)[col:col + m].max(), lim)
+                col += m
+    print("\ncfg2 100 sweeps, vs FP64 (max relative): " + ", ".join(
+        f"{p}: factors {f:.1e} SE {s:.1e} (bound {b:.1e})" for p, (f, s, b) in report.items()))
+    for p, (f, s, b) in report.items():
         assert np.isfinite(f) and np.isfinite(s)
