@@ -198,6 +198,7 @@ jkcals_status make_tc_plan(jkcals_ctx* h) {
     p.tts = 0;
     p.nkt_a = p.n_o = p.o_per_cta = 0;
     p.nbuf = 1;
+    p.nis = 1;
     if (exact && I <= 128) {
       // Two-step form: a narrow mode would reuse each Khatri-Rao entry only BN
       // times; with the largest other mode as a (long exact chains per o) the
@@ -233,6 +234,8 @@ jkcals_status make_tc_plan(jkcals_ctx* h) {
             break;
           }
         }
+        // MMA issuers: one (the ring of 48 KB stages is too shallow to split)
+        p.nis = 1;
         p.nkt = (int64_t)p.n_o * p.nkt_a;
         const int64_t base = (int64_t)p.tiles_c * p.tiles_n;
         const int64_t want = h->opt.splits > 0 ? h->opt.splits : std::max<int64_t>(1, h->num_sms / base);
@@ -393,6 +396,7 @@ jkcals_status enqueue_mttkrp(jkcals_ctx* h, int n, double* const* U, float* cons
   a.n_o = p.n_o;
   a.o_per_cta = p.o_per_cta;
   a.nbuf = p.nbuf;
+  a.nis = p.nis > 0 ? p.nis : 1;
   a.Ia = (int)h->dims[p.a_mode];
   a.ut_stride_a = h->Ipad[p.a_mode];
   a.skip_slice = (p.tts && reuse_slices) ? 1 : 0;

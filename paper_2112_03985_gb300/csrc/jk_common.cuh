@@ -96,6 +96,7 @@ struct TcPlan {
   int n_o;         // values of o
   int o_per_cta;   // o values per CTA (one split)
   int nbuf;        // TMEM accumulator sets (2: the next o accumulates while one drains)
+  int nis;         // MMA-issuing threads (1 or 2; each owns stages / nis ring stages)
   MmaList mma;     // MMAs per K slice
 };
 }  // namespace tc

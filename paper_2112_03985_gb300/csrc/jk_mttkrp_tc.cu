@@ -267,6 +267,31 @@ __device__ __forceinline__ void issue_slice(uint32_t tmem, uint64_t ad0, uint64_
   }
 }
 
+// All MMAs of one stage (K slices kk = 0 .. KS-1), ordered so that the MMAs
+// into one accumulator follow each other: for each (s, t0) of issue_slice the
+// K slices back to back.  On the chain's first stage the s = 0 MMAs of slice 0
+// overwrite their columns; they still come before every other MMA into them.
+template <class Cfg, int G, bool MERGED, int KS>
+__device__ __forceinline__ void issue_stage(uint32_t tmem, uint64_t ad0, uint64_t bd0, uint32_t L, uint32_t b16,
+                                            const uint32_t (&idesc)[5], bool first_stage) {
+  constexpr int P = Cfg::nsplit;
+  constexpr uint32_t a16 = (uint32_t)(128 * Cfg::row_bytes) >> 4;
+#pragma unroll
+  for (int s = 0; s < P; ++s) {
+#pragma unroll
+    for (int t0 = 0; t0 < P - s; t0 += G) {
+      const int cnt = (t0 + G <= P - s) ? G : P - s - t0;
+      const int lev = MERGED ? (s + t0 < 2 ? s + t0 : 2) : s + t0;
+      const bool fresh = s == 0 && (!MERGED || t0 <= 2);
+#pragma unroll
+      for (int kk = 0; kk < KS; ++kk)
+        tc_mma<Cfg::kind>(tmem + (uint32_t)lev * L, ad0 + (uint64_t)(s * a16 + 2 * kk),
+                          bd0 + (uint64_t)((uint32_t)t0 * b16 + 2 * kk), idesc[cnt],
+                          (first_stage && fresh && kk == 0) ? 0u : 1u);
+    }
+  }
+}
+
 // QM: slots for the remaining modes beyond a that the producers track (the
 // column index carry, the factor entries of Q) — 2 covers tensors of up to 4
 // modes with short per-k-step index code, kMaxModes - 2 the rest.
@@ -401,14 +426,14 @@ __global__ void __launch_bounds__(kThreads, 1) mttkrp_tc_kernel(const TcArgs a) 
         tc_fence_after();
         const uint64_t ad0 = desc0 + (uint64_t)(((uint32_t)s * stage_bytes) >> 4);
         const uint64_t bd0 = ad0 + (uint64_t)(a_stage >> 4);
-#pragma unroll
-        for (int kk = 0; kk < ROW / 32; ++kk) {
-          const bool first = kin == 0 && kk == 0;
+        {
+          constexpr int KS = ROW / 32;
+          const bool first = kin == 0;
           switch (variant) {
-            case 4: issue_slice<Cfg, 4, false>(tmem, ad0, bd0, L, b16, idesc, kk, first); break;
-            case 2: issue_slice<Cfg, 2, false>(tmem, ad0, bd0, L, b16, idesc, kk, first); break;
-            case 1: issue_slice<Cfg, 1, false>(tmem, ad0, bd0, L, b16, idesc, kk, first); break;
-            default: issue_slice<Cfg, 1, true>(tmem, ad0, bd0, L, b16, idesc, kk, first); break;
+            case 4: issue_stage<Cfg, 4, false, KS>(tmem, ad0, bd0, L, b16, idesc, first); break;
+            case 2: issue_stage<Cfg, 2, false, KS>(tmem, ad0, bd0, L, b16, idesc, first); break;
+            case 1: issue_stage<Cfg, 1, false, KS>(tmem, ad0, bd0, L, b16, idesc, first); break;
+            default: issue_stage<Cfg, 1, true, KS>(tmem, ad0, bd0, L, b16, idesc, first); break;
           }
         }
         tc_commit(&empty[s]);
@@ -982,8 +1007,8 @@ __global__ void __launch_bounds__(kThreads, 1) mttkrp_tts_kernel(const TcArgs a)
   uint64_t* empty = bars + S;             // stage consumed (the MMAs' commit)
   uint64_t* accum = bars + 2 * S;         // [2] one o's MMAs complete in accumulator set b
   uint64_t* tmem_empty = accum + 2;       // [2] the epilogue warps drained set b
-  uint64_t* drain = accum + 4;            // abort path: the MMAs issued so far are complete
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accum + 5);
+  uint64_t* drain = accum + 4;            // [2] abort path: issuer e's MMAs so far are complete
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accum + 6);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   int* srowexp = const_cast<int*>(abort_flag + 1);   // BN row exponents of this N tile
 
@@ -993,8 +1018,13 @@ __global__ void __launch_bounds__(kThreads, 1) mttkrp_tts_kernel(const TcArgs a)
   const int o1 = o0 + a.o_per_cta < a.n_o ? o0 + a.o_per_cta : a.n_o;
   const int nseg = o1 > o0 ? o1 - o0 : 0;
   const int nkt_a = a.nkt_a;
-  const int nk = nseg * nkt_a;
   const int nbuf = a.nbuf;
+  // nis MMA issuers (1 or 2): issuer e (warp 1 + e) takes the CTA's o's
+  // j = e, e + nis, ... through its own S / nis ring stages; o j accumulates in
+  // set j % nbuf.  With two issuers the tensor pipe runs one issuer's MMAs while
+  // the other commits, waits for its next stage or starts its next o.
+  const int nis = a.nis;
+  const int Sh = S / nis;
   const uint32_t set_cols = (uint32_t)(a.nlev * a.lstride);   // columns of one accumulator set
 
   if (threadIdx.x == 0) {
@@ -1006,7 +1036,8 @@ __global__ void __launch_bounds__(kThreads, 1) mttkrp_tts_kernel(const TcArgs a)
     mbar_init(&accum[1], 1);
     mbar_init(&tmem_empty[0], kEpilogueWarps);
     mbar_init(&tmem_empty[1], kEpilogueWarps);
-    mbar_init(drain, 1);
+    mbar_init(&drain[0], 1);
+    mbar_init(&drain[1], 1);
     *abort_flag = 0;
     fence_barrier_init();
   }
@@ -1022,21 +1053,26 @@ __global__ void __launch_bounds__(kThreads, 1) mttkrp_tts_kernel(const TcArgs a)
 
   if (warp == 0) {
     // ---------------- TMA: lane s loads ring stage s (A image and B image) --------
+    // Stage s belongs to issuer e = s / Sh; it carries that issuer's k-steps
+    // it = s - e Sh, + Sh, ... (k-step kk of its o number it / nkt_a).
     if (lane < S) {
+      const int e = lane / Sh;
+      const int ne = nseg > e ? (nseg - e + nis - 1) / nis : 0;   // o's of issuer e
+      const int nke = ne * nkt_a;
       int issued = 0;
       const unsigned char* srcb = a.Tt + ((int64_t)blockIdx.y * a.nkt + (int64_t)o0 * nkt_a) * (int64_t)b_stage;
       const unsigned char* srca = a.At + (int64_t)blockIdx.x * nkt_a * (int64_t)a_stage;
       unsigned char* dst = ring + (size_t)lane * stage_bytes;
       uint32_t ph = 0;
-      int kk = lane % (nkt_a > 0 ? nkt_a : 1);   // k-step within its o
-      for (int it = lane; it < nk; it += S, ph ^= 1u) {
+      for (int it = lane - e * Sh; it < nke; it += Sh, ph ^= 1u) {
+        const int jj = it / nkt_a;
+        const int kk = it - jj * nkt_a;
+        const int j = e + jj * nis;   // o of the CTA
         if (!wait_bounded(&empty[lane], ph ^ 1u, abort_flag, a.err, 1)) break;
         mbar_arrive_expect_tx(&full[lane], a_stage + b_stage);
         bulk_load(dst, srca + (int64_t)kk * a_stage, a_stage, &full[lane]);
-        bulk_load(dst + a_stage, srcb + (int64_t)it * b_stage, b_stage, &full[lane]);
+        bulk_load(dst + a_stage, srcb + ((int64_t)j * nkt_a + kk) * b_stage, b_stage, &full[lane]);
         issued = it + 1;
-        kk += S;
-        while (kk >= nkt_a) kk -= nkt_a;
       }
       if (*abort_flag && issued > 0) {
         const uint64_t t0 = global_ns();
@@ -1044,9 +1080,12 @@ __global__ void __launch_bounds__(kThreads, 1) mttkrp_tts_kernel(const TcArgs a)
         }
       }
     }
-  } else if (warp == 1) {
-    // ---------------- MMA issuer ----------------------------------------------------
+  } else if (warp == 1 || (warp == 2 && nis == 2)) {
+    // ---------------- MMA issuers ---------------------------------------------------
     if (lane == 0) {
+      const int e = warp - 1;
+      const int ne = nseg > e ? (nseg - e + nis - 1) / nis : 0;
+      const int nke = ne * nkt_a;
       const uint64_t desc0 = smem_desc<ROW>(smem_u32(ring));
       const uint32_t L = (uint32_t)a.lstride, b16 = b_bytes >> 4;
       uint32_t idesc[5];
@@ -1056,47 +1095,49 @@ __global__ void __launch_bounds__(kThreads, 1) mttkrp_tts_kernel(const TcArgs a)
                    (((uint32_t)(c * a.BN) >> 3) << 17) | ((uint32_t)(kRowsM >> 4) << 24);
       const int variant = a.stack >= 4 ? 4 : a.stack;
       bool ok = true;
-      int j = 0, kin = 0, b = 0;   // o (segment), k-step within it, accumulator set
-      uint32_t uses0 = 0, uses1 = 0;   // fills of each accumulator set so far
-      int s = 0;
+      int jj = 0, kin = 0;   // this issuer's o and the k-step within it
+      int j = e, b = e % nbuf;   // o of the CTA and its accumulator set
+      int sp = 0;            // stage within this issuer's ring, and the parity of its pass
       uint32_t ph = 0;
-      for (int it = 0; it < nk && ok; ++it) {
+      for (int it = 0; it < nke && ok; ++it) {
         if (kin == 0 && j >= nbuf) {
-          // set b is refilled once the epilogue drained its previous o
-          ok = wait_bounded(&tmem_empty[b], ((b ? uses1 : uses0) - 1u) & 1u, abort_flag, a.err, 7);
+          // set b is refilled once the epilogue drained its previous o (o j - nbuf,
+          // the set's (j / nbuf)-th use)
+          ok = wait_bounded(&tmem_empty[b], (uint32_t)(j / nbuf - 1) & 1u, abort_flag, a.err, 7);
           if (!ok) break;
         }
-        ok = wait_bounded(&full[s], ph, abort_flag, a.err, 2);
+        const uint32_t td = tmem + (uint32_t)b * set_cols;
+        const int st = e * Sh + sp;
+        ok = wait_bounded(&full[st], ph, abort_flag, a.err, 2);
         if (!ok) break;
         tc_fence_after();
-        const uint64_t ad0 = desc0 + (uint64_t)(((uint32_t)s * stage_bytes) >> 4);
+        const uint64_t ad0 = desc0 + (uint64_t)(((uint32_t)st * stage_bytes) >> 4);
         const uint64_t bd0 = ad0 + (uint64_t)(a_stage >> 4);
-        const uint32_t td = tmem + (uint32_t)b * set_cols;
-#pragma unroll
-        for (int kq = 0; kq < ROW / 32; ++kq) {
-          const bool first = kin == 0 && kq == 0;
+        {
+          constexpr int KS = ROW / 32;
+          const bool first = kin == 0;
           switch (variant) {
-            case 4: issue_slice<Cfg, 4, false>(td, ad0, bd0, L, b16, idesc, kq, first); break;
-            case 2: issue_slice<Cfg, 2, false>(td, ad0, bd0, L, b16, idesc, kq, first); break;
-            default: issue_slice<Cfg, 1, false>(td, ad0, bd0, L, b16, idesc, kq, first); break;
+            case 4: issue_stage<Cfg, 4, false, KS>(td, ad0, bd0, L, b16, idesc, first); break;
+            case 2: issue_stage<Cfg, 2, false, KS>(td, ad0, bd0, L, b16, idesc, first); break;
+            default: issue_stage<Cfg, 1, false, KS>(td, ad0, bd0, L, b16, idesc, first); break;
           }
         }
-        tc_commit(&empty[s]);
+        tc_commit(&empty[st]);
         if (++kin == nkt_a) {
-          tc_commit(&accum[b]);   // this o complete in set b
+          tc_commit(&accum[b]);   // o j complete in set b
           kin = 0;
-          ++j;
-          if (b) ++uses1; else ++uses0;
-          b = (nbuf == 2) ? b ^ 1 : 0;
+          ++jj;
+          j += nis;
+          b = j % nbuf;
         }
-        if (++s == S) {
-          s = 0;
+        if (++sp == Sh) {
+          sp = 0;
           ph ^= 1u;
         }
       }
       if (!ok) {
-        tc_commit(drain);
-        wait_drain(drain, 0);
+        tc_commit(&drain[e]);
+        wait_drain(&drain[e], 0);
       }
     }
   } else if (warp >= kEpilogueWarp0) {
@@ -1125,10 +1166,13 @@ __global__ void __launch_bounds__(kThreads, 1) mttkrp_tts_kernel(const TcArgs a)
         }
       }
     };
-    // this warp's columns: 16-column slices cc = 16 grp + 32 k (BN <= 64: at most 2)
-    float acc_h[32], acc_l[32];
+    // this warp's columns: 16-column slices cc = 16 grp + 32 k (BN <= 64: at most 2),
+    // as 16 pairs of adjacent rows in packed FP32x2 registers: every step below is
+    // the same round-to-nearest operation per lane as the scalar formulas
+    f2 acc_h[16], acc_l[16];
 #pragma unroll
-    for (int r = 0; r < 32; ++r) acc_h[r] = acc_l[r] = 0.f;
+    for (int r = 0; r < 16; ++r) acc_h[r] = acc_l[r] = f2_pack(0.f, 0.f);
+    const f2 m1 = f2_pack(-1.f, -1.f);
     bool ok = true;
     float qh = 0.f, ql = 0.f;
     if (nseg > 0) load_q(o0, qh, ql);
@@ -1146,6 +1190,7 @@ __global__ void __launch_bounds__(kThreads, 1) mttkrp_tts_kernel(const TcArgs a)
       tc_fence_after();
       float qhn = 0.f, qln = 0.f;
       if (j + 1 < nseg) load_q(o0 + j + 1, qhn, qln);   // in flight during this drain
+      const f2 qh2 = f2_pack(qh, qh), ql2 = f2_pack(ql, ql);
 #pragma unroll
       for (int k = 0; k < 2; ++k) {
         const int cc = 16 * grp + 32 * k;
@@ -1158,30 +1203,32 @@ __global__ void __launch_bounds__(kThreads, 1) mttkrp_tts_kernel(const TcArgs a)
           tmem_ld16(col + 3 * L, v3);
           tmem_ld_wait();
 #pragma unroll
-          for (int r = 0; r < 16; ++r) {
+          for (int r = 0; r < 8; ++r) {
             // levels as an FP32 pair (TwoSum; levels 0 and 1 exact, 2 and 3 small)
-            const float l0 = __uint_as_float(v0[r]), l1 = __uint_as_float(v1[r]);
-            const float l2 = __uint_as_float(v2[r]) + __uint_as_float(v3[r]);
-            const float s = __fadd_rn(l0, l1);
-            const float bb = __fsub_rn(s, l0);
-            const float e1 = __fadd_rn(__fsub_rn(l0, __fsub_rn(s, bb)), __fsub_rn(l1, bb));
-            const float t = __fadd_rn(s, l2);
-            const float b2 = __fsub_rn(t, s);
-            const float e2 = __fadd_rn(__fsub_rn(s, __fsub_rn(t, b2)), __fsub_rn(l2, b2));
-            const float lo0 = __fadd_rn(e1, e2);
-            const float hi = __fadd_rn(t, lo0);
-            const float lo = __fsub_rn(lo0, __fsub_rn(hi, t));
+            const f2 l0 = f2_pack(__uint_as_float(v0[2 * r]), __uint_as_float(v0[2 * r + 1]));
+            const f2 l1 = f2_pack(__uint_as_float(v1[2 * r]), __uint_as_float(v1[2 * r + 1]));
+            const f2 l2 = f2_add(f2_pack(__uint_as_float(v2[2 * r]), __uint_as_float(v2[2 * r + 1])),
+                                 f2_pack(__uint_as_float(v3[2 * r]), __uint_as_float(v3[2 * r + 1])));
+            const f2 s_ = f2_add(l0, l1);
+            const f2 bb = f2_sub(s_, l0);
+            const f2 e1 = f2_add(f2_sub(l0, f2_sub(s_, bb)), f2_sub(l1, bb));
+            const f2 t = f2_add(s_, l2);
+            const f2 b2 = f2_sub(t, s_);
+            const f2 e2 = f2_add(f2_sub(s_, f2_sub(t, b2)), f2_sub(l2, b2));
+            const f2 lo0 = f2_add(e1, e2);
+            const f2 hi = f2_add(t, lo0);
+            const f2 lo = f2_sub(lo0, f2_sub(hi, t));
             // times Q (pair): error-free leading product, cross terms
-            const float p = __fmul_rn(hi, qh);
-            const float pe = __fmaf_rn(lo, qh, __fmaf_rn(hi, ql, __fmaf_rn(hi, qh, -p)));
+            const f2 p = f2_mul(hi, qh2);
+            const f2 pe = f2_fma(lo, qh2, f2_fma(hi, ql2, f2_fma(hi, qh2, f2_mul(p, m1))));
             // accumulate (double-float)
-            const int idx = 16 * k + r;
-            const float sh = __fadd_rn(acc_h[idx], p);
-            const float bv = __fsub_rn(sh, acc_h[idx]);
-            const float eh = __fadd_rn(__fsub_rn(acc_h[idx], __fsub_rn(sh, bv)), __fsub_rn(p, bv));
-            const float el = __fadd_rn(eh, __fadd_rn(acc_l[idx], pe));
-            acc_h[idx] = __fadd_rn(sh, el);
-            acc_l[idx] = __fsub_rn(el, __fsub_rn(acc_h[idx], sh));
+            const int idx = 8 * k + r;
+            const f2 sh = f2_add(acc_h[idx], p);
+            const f2 bv = f2_sub(sh, acc_h[idx]);
+            const f2 eh = f2_add(f2_sub(acc_h[idx], f2_sub(sh, bv)), f2_sub(p, bv));
+            const f2 el = f2_add(eh, f2_add(acc_l[idx], pe));
+            acc_h[idx] = f2_add(sh, el);
+            acc_l[idx] = f2_sub(el, f2_sub(acc_h[idx], sh));
           }
         }
       }
@@ -1207,8 +1254,11 @@ __global__ void __launch_bounds__(kThreads, 1) mttkrp_tts_kernel(const TcArgs a)
             int kx = srowexp[cc + r];
             kx = kx < -120 ? -120 : (kx > 120 ? 120 : kx);
             const float sx = pow2f(kx);
-            const int idx = 16 * k + r;
-            out2[i * a.C + c] = ok ? make_float2(acc_h[idx] * sx, acc_l[idx] * sx) : make_float2(0.f, 0.f);
+            float ah0, ah1, al0, al1;
+            f2_unpack(acc_h[8 * k + (r >> 1)], ah0, ah1);
+            f2_unpack(acc_l[8 * k + (r >> 1)], al0, al1);
+            const float ah = (r & 1) ? ah1 : ah0, al = (r & 1) ? al1 : al0;
+            out2[i * a.C + c] = ok ? make_float2(ah * sx, al * sx) : make_float2(0.f, 0.f);
           }
         }
       }
@@ -1358,8 +1408,8 @@ size_t tc_smem_bytes(const TcPlan& p) {
   const size_t row = (size_t)p.row_bytes;
   const size_t a_stage = (size_t)p.nsplit * kRowsM * row;
   const size_t b_stage = (size_t)p.nsplit * p.BN * row;
-  if (p.tts)   // ring | barriers (2 S + 5) | TMEM slot, abort word | row exponents
-    return 1024 + (size_t)p.stages * (a_stage + b_stage) + (2 * p.stages + 5) * 8 + 16 + 4 * (size_t)p.BN;
+  if (p.tts)   // ring | barriers (2 S + 6) | TMEM slot, abort word | row exponents
+    return 1024 + (size_t)p.stages * (a_stage + b_stage) + (2 * p.stages + 6) * 8 + 16 + 4 * (size_t)p.BN;
   return 1024 /*alignment slack*/ + (size_t)p.stages * (a_stage + b_stage) + tc_ua_bytes(p) + (2 * p.stages + 3) * 8 +
          16 + 4 * (size_t)p.BN;
 }

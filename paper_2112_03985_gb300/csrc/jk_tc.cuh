@@ -56,6 +56,7 @@ struct TcArgs {
   // two-step exact form only (TcPlan::tts):
   const unsigned char* At;         // sliced, pre-tiled U_a^T: per 128-row tile and k-step one A stage image
   int nkt_a, n_o, o_per_cta, nbuf;
+  int nis;                         // MMA-issuing threads (1 or 2), each with S / nis ring stages
   int Ia;                          // size of mode a
   int64_t ut_stride_a;             // row stride of UTa / UTa_lo (floats)
   int skip_slice;                  // At already holds the current slices of U_a
