@@ -435,13 +435,15 @@ jkcals_status enqueue_sweep(jkcals_ctx* h) {
       kernels += reuse ? 0 : 1;
     }
     if (h->opt.kernel_timing) JK_CUDA(h, cudaEventRecordWithFlags(h->ev_stop[n], h->stream, cudaEventRecordExternal));
-    // fixed-order split-K reduction into FP64 Mbar_n, then the per-block update
-    JK_TRY(reduce_into(h, n, h->mbuf));
-    UpdateArgs a = update_args(h, n, h->mbuf, kPartF64, 1);
     if (h->plan[n].upd.fused) {
+      // the fused update sums each block's split-K partials itself (fixed order)
+      UpdateArgs a = update_args(h, n, h->part, part_kind(h), mode_splits(h, n));
       JK_CUDA(h, launch_update_fused(a, h->plan[n].upd.fused_smem, h->Rmax, h->uniform_rank, h->stream));
-      kernels += 3;
+      kernels += 2;
     } else {
+      // fixed-order split-K reduction into FP64 Mbar_n, then the two-phase update
+      JK_TRY(reduce_into(h, n, h->mbuf));
+      UpdateArgs a = update_args(h, n, h->mbuf, kPartF64, 1);
       JK_CUDA(h, launch_update(a, h->stream));
       kernels += 4;
     }
@@ -796,7 +798,7 @@ jkcals_status create_impl(jkcals_ctx* h, const void* T, int T_dtype, const int32
     if (h->plan[n].upd.fused) fsmem = std::max(fsmem, h->plan[n].upd.fused_smem);
   if (fsmem > 0) JK_CUDA(h, prepare_update_fused(fsmem, h->Rmax, h->uniform_rank));
   h->kernels_per_sweep = 0;
-  for (int n = 0; n < N; ++n) h->kernels_per_sweep += h->plan[n].upd.fused ? 3 : 4;
+  for (int n = 0; n < N; ++n) h->kernels_per_sweep += h->plan[n].upd.fused ? 2 : 4;
   h->kernels_per_sweep += 1;
   JK_TRY(refresh_factor_state(h));
   if (h->opt.autotune && h->opt.splits <= 0) JK_TRY(autotune_splits(h));

@@ -190,6 +190,40 @@ struct jkcals_ctx {
 
 namespace jk {
 
+// ---- split-K partial sums --------------------------------------------------------
+// Double-float accumulation (unevaluated FP32 pair hi + lo, Knuth TwoSum): about
+// 2^-44 relative, on the FP32 pipe; one conversion to FP64 per output.  GB300
+// issues FP64 (and FP64 conversions) at a small fraction of the FP32 rate, so
+// summing S partials in FP64 would make the reduction FP64-bound.  The
+// reduction kernels and the fused update (which sums a block's partials itself)
+// add the S partials of an element in split order with exactly these steps.
+__device__ __forceinline__ void df_add(float& hi, float& lo, float x) {
+  const float s = __fadd_rn(hi, x);
+  const float bb = __fsub_rn(s, hi);
+  const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(x, bb));
+  lo = __fadd_rn(lo, e);
+  hi = s;
+}
+
+// The double equal to a float (exact), built from its bit pattern with integer
+// operations for zeros and normal numbers (a conversion instruction would run
+// on the narrow FP64 pipe); subnormals, Inf and NaN take the conversion.
+__device__ __forceinline__ double f32_to_f64_exact(float f) {
+  const uint32_t u = __float_as_uint(f);
+  const uint32_t e = (u >> 23) & 0xffu;
+  const unsigned long long sign = (unsigned long long)(u & 0x80000000u) << 32;
+  if ((u & 0x7fffffffu) == 0) return __longlong_as_double((long long)sign);
+  if (e == 0 || e == 255) return (double)f;
+  return __longlong_as_double(
+      (long long)(sign | ((unsigned long long)(e + 896u) << 52) | ((unsigned long long)(u & 0x7fffffu) << 29)));
+}
+
+__device__ __forceinline__ double df_to_double(float hi, float lo) {
+  const float s = __fadd_rn(hi, lo);
+  const float r = __fsub_rn(lo, __fsub_rn(s, hi));
+  return f32_to_f64_exact(s) + f32_to_f64_exact(r);
+}
+
 // ---- error plumbing (jk_capi.cu) --------------------------------------------
 void set_error(const std::string& msg);
 
@@ -273,6 +307,7 @@ cudaError_t launch_update(const UpdateArgs& a, cudaStream_t s);
 size_t update_fused_smem(int64_t I, int Rmax);
 cudaError_t prepare_update_fused(size_t smem, int Rmax, bool uniform_rank);
 cudaError_t launch_update_fused(const UpdateArgs& a, size_t smem, int Rmax, bool uniform_rank, cudaStream_t s);
+
 cudaError_t launch_advance_sweep(int* sweep_idx, cudaStream_t s);
 
 // ---- gradient epilogue (jk_update.cu) ----------------------------------------

@@ -131,24 +131,6 @@ __global__ void reduce_partials_f64_kernel(const double* __restrict__ part, int 
   }
 }
 
-// Double-float accumulation (unevaluated FP32 pair hi + lo, Knuth TwoSum): about
-// 2^-44 relative, on the FP32 pipe; one conversion to FP64 per output.  GB300
-// issues FP64 (and FP64 conversions) at a small fraction of the FP32 rate, so
-// summing S partials in FP64 would make this reduction FP64-bound.
-__device__ __forceinline__ void df_add(float& hi, float& lo, float x) {
-  const float s = __fadd_rn(hi, x);
-  const float bb = __fsub_rn(s, hi);
-  const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(x, bb));
-  lo = __fadd_rn(lo, e);
-  hi = s;
-}
-
-__device__ __forceinline__ double df_to_double(float hi, float lo) {
-  const float s = __fadd_rn(hi, lo);
-  const float r = __fsub_rn(lo, __fsub_rn(s, hi));
-  return (double)s + (double)r;
-}
-
 __global__ void reduce_partials_f32_kernel(const float* __restrict__ part, int S, int64_t count,
                                            double* __restrict__ out) {
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < count;

@@ -1,6 +1,8 @@
 // Fused per-submodel update, one CTA per block (Alg. 3, the loop over p inside
-// the mode loop), all arithmetic in FP64.  Input: the reduced concurrent
-// MTTKRP Mbar_n (I_n x C, FP64, from the fixed-order split-K reduction).
+// the mode loop), all arithmetic in FP64.  Input: the S split-K partials of the
+// concurrent MTTKRP Mbar_n (S x I_n x C: FP64, FP32 or FP32 pairs by form); the
+// block sums the partials of its own rows in split order, with the steps of the
+// reduction kernels, so Mbar_n is the same FP64 value they would give.
 //
 //   H = *_{k != n} G^(k)_g ; L L^T = H            (Hadamard line; Cholesky)
 //   x_i = L^-T L^-1 m_i for every row i            (update line)
@@ -88,7 +90,7 @@ __global__ void __launch_bounds__(NT, FIXED ? 4 : 2) update_fused_kernel(UpdateA
   const int R = FIXED ? RMAX : a.bm.R[g];
   const int off = a.bm.off[g], go = a.bm.gram_off[g];
   const int64_t I = a.I;
-  const double* M = reinterpret_cast<const double*>(a.part);
+  const int64_t count = I * (int64_t)a.C;   // elements of one partial
 
   extern __shared__ double X[];             // I x R rows of this block
   __shared__ double L[RMAX][RMAX + 1];      // H, then its Cholesky factor
@@ -140,17 +142,79 @@ __global__ void __launch_bounds__(NT, FIXED ? 4 : 2) update_fused_kernel(UpdateA
       __syncwarp();
     }
   } else {
-    // warps 1.. : this block's rows of Mbar_n into X (a few rows per thread
-    // with their loads issued before any store)
-    constexpr int kLd = RMAX <= 8 ? 4 : 1;
+    // warps 1.. : this block's rows of Mbar_n into X, each element the sum of its
+    // S partials in split order (a few rows per thread, each split's loads
+    // issued before its adds)
+    constexpr int kLd = RMAX <= 4 ? 4 : (RMAX < 8 ? 2 : 1);
     constexpr int NL = NT - 32;
     for (int64_t i0 = tid - 32; i0 < I; i0 += (int64_t)kLd * NL) {
       double v[kLd][RMAX];
+      // partials loaded PB splits at a time, then added in split order
+      constexpr int PB = RMAX <= 8 ? 2 : 1;
+      if (a.part_kind == kPartF64) {
+        const double* P = reinterpret_cast<const double*>(a.part);
+        for (int s0 = 0; s0 < a.S; s0 += PB) {
+          double t[PB][kLd][RMAX];
 #pragma unroll
-      for (int u = 0; u < kLd; ++u) {
-        const int64_t i = i0 + (int64_t)u * NL;
+          for (int q = 0; q < PB; ++q)
 #pragma unroll
-        for (int r = 0; r < RMAX; ++r) v[u][r] = (i < I && r < R) ? M[i * a.C + off + r] : 0.0;
+            for (int u = 0; u < kLd; ++u) {
+              const int64_t i = i0 + (int64_t)u * NL;
+#pragma unroll
+              for (int r = 0; r < RMAX; ++r)
+                t[q][u][r] = (s0 + q < a.S && i < I && r < R) ? __ldg(P + (s0 + q) * count + i * a.C + off + r) : 0.0;
+            }
+#pragma unroll
+          for (int q = 0; q < PB; ++q)
+            if (s0 + q < a.S) {
+#pragma unroll
+              for (int u = 0; u < kLd; ++u)
+#pragma unroll
+                for (int r = 0; r < RMAX; ++r) v[u][r] = s0 + q == 0 ? t[q][u][r] : v[u][r] + t[q][u][r];
+            }
+        }
+      } else {
+        float hi[kLd][RMAX], lo[kLd][RMAX];
+#pragma unroll
+        for (int u = 0; u < kLd; ++u)
+#pragma unroll
+          for (int r = 0; r < RMAX; ++r) hi[u][r] = lo[u][r] = 0.f;
+        const bool pairs = a.part_kind == kPartF32x2;
+        for (int s0 = 0; s0 < a.S; s0 += PB) {
+          float2 t[PB][kLd][RMAX];
+#pragma unroll
+          for (int q = 0; q < PB; ++q)
+#pragma unroll
+            for (int u = 0; u < kLd; ++u) {
+              const int64_t i = i0 + (int64_t)u * NL;
+#pragma unroll
+              for (int r = 0; r < RMAX; ++r) {
+                t[q][u][r] = make_float2(0.f, 0.f);
+                if (s0 + q < a.S && i < I && r < R) {
+                  const int64_t e = (s0 + q) * count + i * a.C + off + r;
+                  if (pairs)
+                    t[q][u][r] = __ldg(reinterpret_cast<const float2*>(a.part) + e);
+                  else
+                    t[q][u][r].x = __ldg(reinterpret_cast<const float*>(a.part) + e);
+                }
+              }
+            }
+#pragma unroll
+          for (int q = 0; q < PB; ++q)
+            if (s0 + q < a.S) {
+#pragma unroll
+              for (int u = 0; u < kLd; ++u)
+#pragma unroll
+                for (int r = 0; r < RMAX; ++r) {
+                  df_add(hi[u][r], lo[u][r], t[q][u][r].x);
+                  if (pairs) lo[u][r] = __fadd_rn(lo[u][r], t[q][u][r].y);
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kLd; ++u)
+#pragma unroll
+          for (int r = 0; r < RMAX; ++r) v[u][r] = df_to_double(hi[u][r], lo[u][r]);
       }
 #pragma unroll
       for (int u = 0; u < kLd; ++u) {
@@ -326,6 +390,340 @@ __global__ void __launch_bounds__(NT, FIXED ? 4 : 2) update_fused_kernel(UpdateA
   }
 }
 
+// Wide form of the same update for ranks <= 7: one CTA per block, warp 0 forms
+// H and its Cholesky factor while up to 224 row threads (one or two rows each, or more)
+// sum their rows' split-K partials; then every row thread solves its rows and
+// keeps its contributions to the Gram entries G_ab (a <= b) and to sum(x * m)
+// in registers.  A reduce-scatter across the lanes of each warp (halving the
+// number of values per lane at each of five shuffle steps: about NPAD adds per
+// lane instead of 5 NPAD for a plain butterfly) and a fixed-order sum over the
+// warps give the Gram and the fit term; all arithmetic stays in FP64 and the
+// order of every sum is fixed (deterministic).  One row per thread shortens
+// each block's chain of dependent FP64 operations, which bounds the
+// narrow-row-count updates.
+constexpr int kWideRows = 224;   // row threads per CTA at most (two CTAs of rank 5 fit an SM)
+
+__host__ __device__ constexpr int wide_npad(int rmax) {
+  return rmax * (rmax + 1) / 2 + 1 <= 16 ? 16 : 32;
+}
+
+template <int RMAX, bool FIXED>
+__global__ void __launch_bounds__(kWideRows + 32, 1) update_wide_kernel(UpdateArgs a) {
+  constexpr int NP = RMAX * (RMAX + 1) / 2;   // Gram entries (upper triangle), then the fit term
+  constexpr int NPAD = wide_npad(RMAX);
+  const int g = blockIdx.x;
+  const int tid = threadIdx.x;
+  const int lane = tid & 31, warp = tid >> 5;
+  const int RT = (int)blockDim.x - 32;        // row threads
+  const bool last = (a.n == a.N - 1);
+  const int sweep = last ? *a.sweep_idx : 0;
+  const double qnan = __longlong_as_double(0x7ff8000000000000LL);
+  if (a.status[g] != 0) {
+    if (last && tid == 0 && a.loss_hist != nullptr && sweep < a.loss_cap) a.loss_hist[(int64_t)sweep * a.K + g] = qnan;
+    return;
+  }
+  const int R = FIXED ? RMAX : a.bm.R[g];
+  const int off = a.bm.off[g], go = a.bm.gram_off[g];
+  const int64_t I = a.I;
+  const int64_t count = I * (int64_t)a.C;   // elements of one partial
+
+  extern __shared__ double X[];             // I x R rows of this block (Mbar rows, then the solutions)
+  __shared__ double L[RMAX][RMAX + 1];
+  __shared__ double Hc[RMAX * RMAX];
+  __shared__ double invd[RMAX];
+  __shared__ double scale[RMAX];
+  __shared__ double wsum[(kWideRows + 32) / 32][NPAD];
+  __shared__ double tot[NPAD];
+  __shared__ int spd_ok;
+  __shared__ int colmax[RMAX];
+
+  if (tid < RMAX) colmax[tid] = 0;
+  if (warp == 0) {
+    if (lane == 0) spd_ok = 1;
+    for (int p = lane; p < R * R; p += 32) {
+      double h = 1.0;
+      for (int k = 0; k < a.N; ++k)
+        if (k != a.n) h *= a.gram[k][go + p];
+      L[p / R][p % R] = h;
+      Hc[p] = h;
+    }
+    __syncwarp();
+    for (int j = 0; j < R; ++j) {
+      if (lane == 0) {
+        double d = L[j][j];
+        for (int k = 0; k < j; ++k) d -= L[j][k] * L[j][k];
+        if (!(d > 0.0) || !isfinite(d)) {
+          spd_ok = 0;
+          d = 1.0;
+        }
+        const double rs = rsqrt(d);
+        L[j][j] = d * rs;
+        invd[j] = rs;
+      }
+      __syncwarp();
+      const int i = j + 1 + lane;
+      if (i < R) {
+        double v = L[i][j];
+        for (int k = 0; k < j; ++k) v -= L[i][k] * L[j][k];
+        L[i][j] = v * invd[j];
+      }
+      __syncwarp();
+    }
+  } else {
+    // the block's rows of Mbar_n: each element the sum of its S partials in split
+    // order; the partials are loaded PB splits at a time (all in flight together)
+    // and then added in order, one memory round trip per batch
+    constexpr int PB = RMAX <= 4 ? 8 : 4;
+    for (int64_t i = tid - 32; i < I; i += RT) {
+      double v[RMAX];
+      if (a.part_kind == kPartF64) {
+        const double* P = reinterpret_cast<const double*>(a.part);
+#pragma unroll
+        for (int r = 0; r < RMAX; ++r) v[r] = 0.0;
+        for (int s0 = 0; s0 < a.S; s0 += PB) {
+          double t[PB][RMAX];
+#pragma unroll
+          for (int u = 0; u < PB; ++u)
+#pragma unroll
+            for (int r = 0; r < RMAX; ++r)
+              t[u][r] = (s0 + u < a.S && r < R) ? __ldg(P + (s0 + u) * count + i * a.C + off + r) : 0.0;
+#pragma unroll
+          for (int u = 0; u < PB; ++u)
+            if (s0 + u < a.S) {
+#pragma unroll
+              for (int r = 0; r < RMAX; ++r) v[r] = s0 + u == 0 ? t[u][r] : v[r] + t[u][r];
+            }
+        }
+      } else {
+        float hi[RMAX], lo[RMAX];
+#pragma unroll
+        for (int r = 0; r < RMAX; ++r) hi[r] = lo[r] = 0.f;
+        const bool pairs = a.part_kind == kPartF32x2;
+        for (int s0 = 0; s0 < a.S; s0 += PB) {
+          float2 t[PB][RMAX];
+#pragma unroll
+          for (int u = 0; u < PB; ++u)
+#pragma unroll
+            for (int r = 0; r < RMAX; ++r) {
+              t[u][r] = make_float2(0.f, 0.f);
+              if (s0 + u < a.S && r < R) {
+                const int64_t e = (s0 + u) * count + i * a.C + off + r;
+                if (pairs)
+                  t[u][r] = __ldg(reinterpret_cast<const float2*>(a.part) + e);
+                else
+                  t[u][r].x = __ldg(reinterpret_cast<const float*>(a.part) + e);
+              }
+            }
+#pragma unroll
+          for (int u = 0; u < PB; ++u)
+            if (s0 + u < a.S) {
+#pragma unroll
+              for (int r = 0; r < RMAX; ++r) {
+                df_add(hi[r], lo[r], t[u][r].x);
+                if (pairs) lo[r] = __fadd_rn(lo[r], t[u][r].y);
+              }
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < RMAX; ++r) v[r] = df_to_double(hi[r], lo[r]);
+      }
+#pragma unroll
+      for (int r = 0; r < RMAX; ++r)
+        if (r < R) X[i * R + r] = v[r];
+    }
+  }
+  __syncthreads();
+  if (!spd_ok) {
+    if (tid == 0) {
+      atomicOr(&a.status[g], (int)JKCALS_BLOCK_NOT_SPD);
+      if (last && a.loss_hist != nullptr && sweep < a.loss_cap) a.loss_hist[(int64_t)sweep * a.K + g] = qnan;
+    }
+    return;
+  }
+
+  // solve this thread's rows; Gram and fit contributions in registers
+  double acc[NPAD];
+#pragma unroll
+  for (int p = 0; p < NPAD; ++p) acc[p] = 0.0;
+  if (warp > 0) {
+    for (int64_t i = tid - 32; i < I; i += RT) {
+      double x[RMAX], m[RMAX];
+#pragma unroll
+      for (int r = 0; r < RMAX; ++r) m[r] = (r < R) ? X[i * R + r] : 0.0;
+      if (a.n == a.n_hat && left_out(a.bm, g, i)) {
+#pragma unroll
+        for (int r = 0; r < RMAX; ++r) x[r] = 0.0;
+      } else {
+#pragma unroll
+        for (int r = 0; r < RMAX; ++r) {
+          if (r < R) {
+            double v = m[r];
+#pragma unroll
+            for (int k = 0; k < r; ++k) v -= L[r][k] * x[k];
+            x[r] = v * invd[r];
+          } else {
+            x[r] = 0.0;
+          }
+        }
+#pragma unroll
+        for (int r = RMAX - 1; r >= 0; --r) {
+          if (r < R) {
+            double v = x[r];
+#pragma unroll
+            for (int k = r + 1; k < RMAX; ++k)
+              if (k < R) v -= L[k][r] * x[k];
+            x[r] = v * invd[r];
+          }
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < RMAX; ++r)
+        if (r < R) X[i * R + r] = x[r];
+      int p = 0;
+#pragma unroll
+      for (int r0 = 0; r0 < RMAX; ++r0)
+#pragma unroll
+        for (int r1 = r0; r1 < RMAX; ++r1) acc[p] = fma(x[r0], x[r1], acc[p]), ++p;   // zero beyond R
+      if (last) {
+#pragma unroll
+        for (int r = 0; r < RMAX; ++r) acc[NP] = fma(x[r], m[r], acc[NP]);
+      }
+    }
+  }
+  // reduce-scatter across the warp: at the step with lane offset o a lane keeps
+  // the half of its values that its bit o selects and adds its partner's copy
+#pragma unroll
+  for (int st = 0; st < 5; ++st) {
+    const int o = 16 >> st;
+    const bool up = (lane & o) != 0;
+    const int half = NPAD >> (st + 1);
+    if (half >= 1) {
+#pragma unroll
+      for (int j = 0; j < NPAD / 2; ++j) {
+        if (j < half) {
+          const double send = up ? acc[j] : acc[half + j];
+          const double keep = up ? acc[half + j] : acc[j];
+          acc[j] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+        }
+      }
+    } else {
+      acc[0] = acc[0] + __shfl_xor_sync(0xffffffffu, acc[0], o);
+    }
+  }
+  {
+    // the entries this lane now holds: base index from its lane bits, then j
+    constexpr int KEEP = NPAD >= 32 ? NPAD / 32 : 1;
+    int base = 0;
+#pragma unroll
+    for (int st = 0; st < 5; ++st) {
+      const int half = NPAD >> (st + 1);
+      if (half >= 1 && (lane & (16 >> st))) base += half;
+    }
+    if (NPAD >= 32 || (lane & 1) == 0) {
+#pragma unroll
+      for (int j = 0; j < KEEP; ++j) wsum[warp][base + j] = acc[j];
+    }
+  }
+  __syncthreads();
+  const int nw = (int)blockDim.x >> 5;
+  if (tid <= NP) {
+    double sacc = wsum[0][tid];
+    for (int w = 1; w < nw; ++w) sacc += wsum[w][tid];
+    tot[tid] = sacc;
+  }
+  __syncthreads();
+
+  // normalisation (modes n < N-1): unit columns, norm dropped
+  const bool norm = a.normalise && a.n < a.N - 1;
+  auto gidx = [&](int r0, int r1) {   // position of G(r0, r1), r0 <= r1, in the packed upper triangle
+    return r0 * RMAX - r0 * (r0 - 1) / 2 + (r1 - r0);
+  };
+  if (tid < R) {
+    double sc = 1.0;
+    if (norm) {
+      const double v = sqrt(tot[gidx(tid, tid)]);
+      sc = (v > 0.0) ? 1.0 / v : 1.0;
+    }
+    scale[tid] = sc;
+  }
+  __syncthreads();
+
+  // the factor block: FP64 row-major, the transposed FP32 hi/lo copies and the
+  // column maxima of the high parts
+  float cm[RMAX];
+#pragma unroll
+  for (int r = 0; r < RMAX; ++r) cm[r] = 0.f;
+  if (warp > 0) {
+    for (int64_t i = tid - 32; i < I; i += RT) {
+#pragma unroll
+      for (int r = 0; r < RMAX; ++r) {
+        if (r < R) {
+          const double x = norm ? X[i * R + r] * scale[r] : X[i * R + r];
+          a.U[i * a.C + off + r] = x;
+          if (a.UT != nullptr) {
+            float hi, lo;
+            split_f32_pair(x, hi, lo);
+            a.UT[(int64_t)(off + r) * a.I_pad + i] = hi;
+            if (a.UT_lo != nullptr) a.UT_lo[(int64_t)(off + r) * a.I_pad + i] = lo;
+            cm[r] = fmaxf(cm[r], fabsf(hi));
+          }
+        }
+      }
+    }
+  }
+  if (a.UT != nullptr && a.cmax != nullptr) {
+#pragma unroll
+    for (int r = 0; r < RMAX; ++r) {
+      float v = cm[r];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+      if (lane == 0 && r < R) atomicMax(&colmax[r], __float_as_int(v));
+    }
+    __syncthreads();
+    if (tid < R) a.cmax[off + tid] = __int_as_float(colmax[tid]);
+  }
+  // the refreshed Gram, scaled like the columns
+  for (int p = tid; p < R * R; p += blockDim.x) {
+    const int r0 = p / R, r1 = p % R;
+    const double v = tot[r0 <= r1 ? gidx(r0, r1) : gidx(r1, r0)];
+    a.gram_n[go + p] = norm ? v * scale[r0] * scale[r1] : v;
+  }
+  if (!last || tid != 0) return;
+
+  // e_g = ||T_{-g}||^2 + sum(H * G) - 2 sum(x * m)
+  double hg = 0.0;
+  for (int p = 0; p < R * R; ++p) {
+    const int r0 = p / R, r1 = p % R;
+    hg = fma(Hc[p], tot[r0 <= r1 ? gidx(r0, r1) : gidx(r1, r0)], hg);
+  }
+  const double nt = a.normT2[g];
+  const double e = nt + (hg - 2.0 * tot[NP]);
+  a.loss_last[g] = e;
+  if (a.loss_hist != nullptr && sweep < a.loss_cap) a.loss_hist[(int64_t)sweep * a.K + g] = e;
+  const double tol = *a.tol;
+  const double prev = a.loss_prev[g];
+  if (tol > 0.0 && isfinite(prev) && fabs(prev - e) / nt < tol) a.status[g] |= JKCALS_BLOCK_CONVERGED;
+  a.loss_prev[g] = e;
+}
+
+template <int RM, bool F>
+cudaError_t run_wide(const UpdateArgs* a, size_t smem, cudaStream_t s, bool prepare) {
+  if (prepare) {
+    cudaFuncAttributes fa;
+    const cudaError_t e = cudaFuncGetAttributes(&fa, update_wide_kernel<RM, F>);
+    if (e != cudaSuccess) return e;
+    if ((size_t)fa.maxDynamicSharedSizeBytes >= smem) return cudaSuccess;
+    return cudaFuncSetAttribute(update_wide_kernel<RM, F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  }
+  // one row per thread for narrow modes (their updates are bound by one block's
+  // chain of dependent operations), two for wider ones (fewer warps, so fewer
+  // FP64 adds in the cross-lane reduction of the Gram)
+  int64_t rt = a->I <= 128 ? (a->I + 31) / 32 * 32 : ((a->I + 1) / 2 + 31) / 32 * 32;
+  if (rt > kWideRows) rt = kWideRows;
+  update_wide_kernel<RM, F><<<a->K, (unsigned)(rt + 32), smem, s>>>(*a);
+  return cudaGetLastError();
+}
+
 // Instances: exact ranks 1..8 when all blocks share one rank, otherwise the
 // rank classes 8, 16, 32 with per-rank guards.
 template <int RM, bool F>
@@ -347,13 +745,13 @@ static cudaError_t dispatch_fused(const UpdateArgs* a, size_t smem, int Rmax, bo
                                   bool prepare) {
   if (uniform) {
     switch (Rmax) {
-      case 1: return run_fused<1, true>(a, smem, s, prepare);
-      case 2: return run_fused<2, true>(a, smem, s, prepare);
-      case 3: return run_fused<3, true>(a, smem, s, prepare);
-      case 4: return run_fused<4, true>(a, smem, s, prepare);
-      case 5: return run_fused<5, true>(a, smem, s, prepare);
-      case 6: return run_fused<6, true>(a, smem, s, prepare);
-      case 7: return run_fused<7, true>(a, smem, s, prepare);
+      case 1: return run_wide<1, true>(a, smem, s, prepare);
+      case 2: return run_wide<2, true>(a, smem, s, prepare);
+      case 3: return run_wide<3, true>(a, smem, s, prepare);
+      case 4: return run_wide<4, true>(a, smem, s, prepare);
+      case 5: return run_wide<5, true>(a, smem, s, prepare);
+      case 6: return run_wide<6, true>(a, smem, s, prepare);
+      case 7: return run_wide<7, true>(a, smem, s, prepare);
       case 8: return run_fused<8, true>(a, smem, s, prepare);
       default: break;
     }
@@ -366,6 +764,7 @@ static cudaError_t dispatch_fused(const UpdateArgs* a, size_t smem, int Rmax, bo
 }  // namespace
 
 size_t update_fused_smem(int64_t I, int Rmax) { return (size_t)I * Rmax * sizeof(double); }
+
 
 cudaError_t prepare_update_fused(size_t smem, int Rmax, bool uniform) {
   return dispatch_fused(nullptr, smem, Rmax, uniform, nullptr, true);
