@@ -120,6 +120,10 @@ def roofline_peak(precision, peaks, sustained=False):
     raise ValueError(precision)
 
 
+# Bytes per tensor element of the copy of T_(n) that a form's MTTKRP streams (the
+# pre-tiled parts; FP64: the FP64 unfolding).
+FORM_TENSOR_BYTES = {"fp64": 8, "tf32": 4, "3xtf32": 8, "bf16": 2, "split_bf16": 6, "exact_bf16": 8}
+
 # Tensor-core products issued per useful multiply-add, per form (part products of the split forms).
 ISSUED_PER_USEFUL = {"fp64": 1, "tf32": 1, "bf16": 1, "3xtf32": 3, "split_bf16": 6, "exact_bf16": 10}
 
@@ -737,7 +741,8 @@ def cfg3_arm(args):
         raise RuntimeError("bench.py needs a CUDA device (there is no CPU fallback)")
     peaks, peak_src = load_peaks()
     w = W.make_config(3, R=args.rank)
-    flops = 2.0 * w.C * float(np.prod(w.T.shape))
+    elems = float(np.prod(w.T.shape))
+    flops = 2.0 * w.C * elems
     forms = {}
     for prec in ("fp64", "tf32", "3xtf32", "bf16", "split_bf16", "exact_bf16"):
         with api.from_workload(w, precision=prec, device="cuda", kernel_timing=True) as h:
@@ -753,14 +758,25 @@ def cfg3_arm(args):
             kt = np.median(np.array(times), axis=0)
             _, splits = h.sweep_info()
         tf = [flops / (t * 1e-3) / 1e12 for t in kt]
-        _, peak, note = roofline_peak(prec, peaks)
+        bound, peak, note = roofline_peak(prec, peaks)
+        # the two floors of one launch: the form's tensor (or FP64) work at its
+        # peak, and one read of its copy of the tensor at the measured HBM rate
+        t_compute = flops / (peak * 1e12)
+        t_hbm = elems * FORM_TENSOR_BYTES[prec] / (peaks["hbm_gbs"] * 1e9)
+        binding = "hbm" if t_hbm > t_compute else bound
+        floor = max(t_compute, t_hbm)
         forms[prec] = {"mttkrp_ms": [round(float(t), 4) for t in kt], "mttkrp_tflops": [round(x, 2) for x in tf],
                        "frac_of_peak": [round(x / peak, 3) for x in tf], "peak_tflops": peak, "peak": note,
+                       "tensor_bytes_per_elem": FORM_TENSOR_BYTES[prec],
+                       "floor_us": {"compute": round(1e6 * t_compute, 1), "hbm": round(1e6 * t_hbm, 1)},
+                       "bound": binding, "frac_of_roofline": [round(floor / (t * 1e-3), 3) for t in kt],
                        "splits": list(splits), "sweep_ms": round(sweep_ms, 3),
                        "submodel_iters_per_s": w.K / (sweep_ms * 1e-3)}
     out = {"metric": "concurrent MTTKRP TFLOP/s per precision form (configuration 3)", "unit": "TFLOP/s",
            "config": {"workload": f"400x400x400 FP32, R={args.rank}, delete-10 x 40 groups", "C": w.C,
-                      "useful_gflop_per_mode": flops / 1e9, "peaks": peak_src},
+                      "useful_gflop_per_mode": flops / 1e9, "peaks": peak_src,
+                      "roofline": "per launch: max(useful flops x issued passes / measured peak of the form, "
+                                  "tensor bytes of the form / measured HBM GB/s); frac = that floor / time"},
            "forms": forms}
     print(json.dumps(out), flush=True)
 
