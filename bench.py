@@ -51,6 +51,8 @@ def parse():
                         "on 400^3 delete-10 (R = --rank); 4: the batch of 64 uneven problems "
                         "(batched 3xTF32 + autotuner vs one launch per problem in FP64)")
     p.add_argument("--rank", type=int, default=10, help="configuration 3 rank (5, 10 or 20)")
+    p.add_argument("--tol-run", action="store_true",
+                   help="the 300x100x50 workload to convergence: tol 1e-6, at most 1000 sweeps (Sec. 5.2)")
     p.add_argument("--probe-peaks", action="store_true",
                    help="measure the FP64 / FP32 / TF32 / BF16 matmul peaks of this GPU (prints JSON)")
     p.add_argument("--rank-sweep", action="store_true",
@@ -781,6 +783,43 @@ def cfg3_arm(args):
     print(json.dumps(out), flush=True)
 
 
+def tol_run_arm(args):
+    """--tol-run: the 300x100x50 workload run to convergence, the setting of the paper's
+    real-data runs (Sec. 5.2): tol 1e-6 on |e_prev - e| / ||T_g||^2, at most 1000 sweeps;
+    every block frozen once it converges.  Reports the sweeps each submodel took and the
+    rate of submodel sweeps actually run (frozen blocks excluded)."""
+    import numpy as np
+    import torch
+
+    from paper_2112_03985_gb300 import api, workloads as W
+
+    if not torch.cuda.is_available():
+        raise RuntimeError("bench.py needs a CUDA device (there is no CPU fallback)")
+    w = W.make_config(2)
+    tol, cap = 1e-6, 1000
+    T32 = torch.from_numpy(np.ascontiguousarray(w.T.astype(np.float32))).cuda()
+    init = [torch.from_numpy(u).cuda() for u in api.multi_init(w.init)]
+    res = []
+    for _ in range(2):   # the first run warms up (graph capture, clocks)
+        with api.JKCALS(T32, w.n_hat, w.ranks, w.left_out, init, precision=args.precision) as h:
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            done, final = h.run(cap, tol=tol)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            per = h.run_block_sweeps()
+            st = h.block_status()
+        res.append((done, per, st, dt))
+    done, per, st, dt = res[-1]
+    out = {"metric": "JK-CALS run to convergence (configuration 2)", "unit": "submodel-iters/s",
+           "value": float(per.sum()) / dt, "precision": args.precision, "tol": tol, "max_sweeps": cap,
+           "sweeps_run": int(done), "seconds": dt,
+           "sweeps_per_submodel": {"min": int(per.min()), "median": float(np.median(per)), "max": int(per.max())},
+           "converged": int(np.count_nonzero(st & 2)), "submodels": w.K,
+           "timing": "wall clock of jkcals_run (host checks every 16 sweeps, graph replays in between)"}
+    print(json.dumps(out), flush=True)
+
+
 RANK_SWEEP_C = (1, 2, 5, 10, 20, 50, 100, 200, 500, 1000, 2000)
 RANK_SWEEP_FORMS = ("fp64", "tf32", "3xtf32", "bf16", "split_bf16", "exact_bf16")
 
@@ -854,6 +893,9 @@ def main():
         return
     if args.probe_peaks:
         probe_peaks_arm(args)
+        return
+    if args.tol_run:
+        tol_run_arm(args)
         return
     if args.rank_sweep:
         rank_sweep_arm(args)

@@ -256,6 +256,14 @@ jkcals_status jkcals_plan_query(int N, const int64_t* dims, int K, const int32_t
 jkcals_status jkcals_run(jkcals_t h, int max_sweeps, double tol, int* sweeps_done,
                          double* final_loss);
 
+/*
+ * Sweeps each block ran in the latest jkcals_run (K int32, host): a block that
+ * converged (or met a non-positive pivot) stops counting at the sweep that
+ * froze it -- with tol > 0 the sweep count at which the stopping rule of Alg. 1
+ * (Sec. 3.2) held for it.  JKCALS_ERR_STATE before the first jkcals_run.
+ */
+jkcals_status jkcals_run_block_sweeps(jkcals_t h, int32_t* sweeps);
+
 /* Copy the current multi-matrices out: U[n] is I_n x C row-major FP64 (host or device). */
 jkcals_status jkcals_get_factors(jkcals_t h, double* const* U);
 

@@ -44,6 +44,7 @@ SIGNATURES = {
     "jkcals_mode_plan": (ct.c_int, [P, ct.c_int, ct.POINTER(ct.c_int), ct.POINTER(ct.c_int), ct.POINTER(ct.c_int),
                                     ct.POINTER(ct.c_int)]),
     "jkcals_run": (ct.c_int, [P, ct.c_int, ct.c_double, ct.POINTER(ct.c_int), P]),
+    "jkcals_run_block_sweeps": (ct.c_int, [P, I32P]),
     "jkcals_get_factors": (ct.c_int, [P, PP]),
     "jkcals_set_factors": (ct.c_int, [P, PP]),
     "jkcals_get_block_status": (ct.c_int, [P, I32P]),

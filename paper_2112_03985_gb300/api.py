@@ -193,6 +193,14 @@ class JKCALS:
             L.check(st, "jkcals_run")
         return done.value, fl
 
+    def run_block_sweeps(self):
+        """Sweeps each block ran in the latest run() (K ints): where a block converged
+        (or met a non-positive pivot) and was frozen."""
+        out = np.empty(self.K, dtype=np.int32)
+        L.check(self._lib.jkcals_run_block_sweeps(self._h, out.ctypes.data_as(ct.POINTER(ct.c_int32))),
+                "jkcals_run_block_sweeps")
+        return out
+
     def get_factors_into(self, outs):
         return self.get_factors(outs=outs)
 

@@ -5,6 +5,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 #include <numeric>
 #include <string>
 #include <vector>
@@ -1212,13 +1213,21 @@ jkcals_status jkcals_run(jkcals_t h, int max_sweeps, double tol, int* sweeps_don
   JK_CUDA(h, cudaMemcpyAsync(h->d_tol, &h->tol_host, sizeof(double), cudaMemcpyHostToDevice, h->stream));
   int done = 0;
   std::vector<int32_t> st(h->K);
+  std::vector<double> lh((size_t)chunk * h->K);
+  h->run_block_sweeps.assign(h->K, 0);
   while (done < max_sweeps) {
     const int n = std::min(chunk, max_sweeps - done);
     JK_CUDA(h, cudaMemsetAsync(h->d_sweep_idx, 0, sizeof(int), h->stream));
     JK_TRY(run_sweeps(h, n));
     done += n;
     JK_CUDA(h, cudaMemcpyAsync(st.data(), h->d_status, sizeof(int32_t) * h->K, cudaMemcpyDeviceToHost, h->stream));
+    // a block's loss is NaN in the sweeps after it froze: its sweeps are the finite ones
+    JK_CUDA(h, cudaMemcpyAsync(lh.data(), h->loss_hist, sizeof(double) * n * h->K, cudaMemcpyDeviceToHost,
+                               h->stream));
     JK_CUDA(h, cudaStreamSynchronize(h->stream));
+    for (int t = 0; t < n; ++t)
+      for (int g = 0; g < h->K; ++g)
+        if (std::isfinite(lh[(size_t)t * h->K + g])) ++h->run_block_sweeps[g];
     bool all_frozen = true;
     for (int32_t v : st) all_frozen = all_frozen && (v != 0);
     if (all_frozen) break;
@@ -1228,6 +1237,14 @@ jkcals_status jkcals_run(jkcals_t h, int max_sweeps, double tol, int* sweeps_don
   if (sweeps_done) *sweeps_done = done;
   if (final_loss) JK_TRY(copy_out(h, final_loss, h->d_loss_last, sizeof(double) * h->K));
   return any_not_spd(h);
+}
+
+jkcals_status jkcals_run_block_sweeps(jkcals_t h, int32_t* sweeps) {
+  JK_TRY(check_handle(h));
+  if (sweeps == nullptr) return fail(JKCALS_ERR_ARG, "sweeps is NULL");
+  if ((int)h->run_block_sweeps.size() != h->K) return fail(JKCALS_ERR_STATE, "no jkcals_run on this handle yet");
+  std::copy(h->run_block_sweeps.begin(), h->run_block_sweeps.end(), sweeps);
+  return JKCALS_OK;
 }
 
 jkcals_status jkcals_get_factors(jkcals_t h, double* const* U) {

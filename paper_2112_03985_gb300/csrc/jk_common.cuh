@@ -178,6 +178,7 @@ struct jkcals_ctx {
   float* gcmax[jk::kMaxModes] = {nullptr};
   int* rowexp[jk::kMaxModes] = {nullptr};    // row exponents of T_(n) (exact-chain grid)
   int* d_err = nullptr;                      // bounded-wait expiry code of the TC kernel
+  std::vector<int32_t> run_block_sweeps;     // sweeps each block ran in the latest jkcals_run
 
   cudaGraphExec_t sweep_exec = nullptr;
   bool graph_valid = false;

@@ -117,6 +117,14 @@ def group_blocks(I_hat: int, d: int) -> List[np.ndarray]:
     return [np.arange(g * d, (g + 1) * d, dtype=np.int64) for g in range(I_hat // d)]
 
 
+def all_ranks_blocks(I_hat: int, ranks=(3, 5, 7, 9)):
+    """The "All" layout of Sec. 5.1: every left-out sample jackknifed with one model
+    per rank in ``ranks``, side by side in one concurrent fit.  Returns (blocks, ranks)
+    with block k leaving out sample k // len(ranks) at rank ranks[k % len(ranks)]."""
+    blocks = [np.array([p], dtype=np.int64) for p in range(I_hat) for _ in ranks]
+    return blocks, [int(r) for _ in range(I_hat) for r in ranks]
+
+
 def make_workload(name, dims, R, *, n_hat=0, blocks=None, noise=0.01, seed=0,
                   sweeps=10, dtype="f64", factor_kind="uniform", init_kind="uniform",
                   ranks=None):

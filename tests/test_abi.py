@@ -61,7 +61,8 @@ def test_options_struct_layout_matches_header():
 
 
 HANDLE_CALLS = ["jkcals_mttkrp", "jkcals_als_sweep", "jkcals_als_sweep_async", "jkcals_kernel_times",
-                "jkcals_sweep_info", "jkcals_mode_plan", "jkcals_jackknife_se", "jkcals_run", "jkcals_get_factors",
+                "jkcals_sweep_info", "jkcals_mode_plan", "jkcals_jackknife_se", "jkcals_run", "jkcals_run_block_sweeps",
+                "jkcals_get_factors",
                 "jkcals_set_factors", "jkcals_get_block_status", "jkcals_grad", "jkcals_loss_history", "jkcals_sync"]
 
 

@@ -1,0 +1,110 @@
+"""Tolerance-driven runs and several ranks per left-out sample (Sec. 5.1 "All", Sec. 5.2
+stopping rule), against the oracle.
+
+* "All": every left-out sample of a 12x30x40 tensor (planted rank 7, 1% noise) is
+  jackknifed with models of rank 3, 5, 7 and 9 in one handle (48 blocks, C = 288);
+  each block must follow its own JK-ALS run (Alg. 2) in the oracle.  Bars: FP64 form
+  1e-10 on factors element by element and on losses (noise floor of this case: 1e-16
+  perturbations move the factors by at most 5e-13 over 20 sweeps); exact-chain form
+  1e-6 on factors and the derived loss bound after every sweep.
+* Tolerance runs (jkcals_run): a block stops when |e_prev - e| / ||T_g||^2 < tol and is
+  frozen; the sweep at which each sampled block stopped must equal the oracle's
+  (FP64 form), or be within one sweep of it for the exact-chain form on the
+  300x100x50 workload at tol 1e-6 and at most 1000 sweeps (the paper's real-data
+  setting), where a loss within its error of the threshold may cross it one sweep
+  earlier or later.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2112_03985_gb300 import api, workloads as W
+
+from _helpers import assert_factors, stepwise_loss_check
+
+pytestmark = pytest.mark.gpu
+
+
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def _all_workload(sweeps=20):
+    blocks, ranks = W.all_ranks_blocks(12, (3, 5, 7, 9))
+    return W.make_workload("all 12x30x40 R3-9", (12, 30, 40), 7, blocks=blocks, ranks=ranks, noise=0.01,
+                           seed=70, sweeps=sweeps)
+
+
+def test_all_ranks_per_sample_fp64_every_block():
+    _cuda()
+    w = _all_workload()
+    with api.from_workload(w) as h:
+        L = h.als_sweep(w.sweeps)
+        U = h.get_factors()
+        st = h.block_status()
+    assert np.all(st == 0)
+    sel = list(range(w.K))
+    ora = O.jk_als(w.T, w.n_hat, w.left_out, w.init, w.sweeps, blocks=sel)
+    errs = assert_factors(w, U, ora.factors, sel, 1e-10)
+    np.testing.assert_allclose(L, ora.losses, rtol=1e-10)
+    print(f"\n'All' FP64, 48 blocks of ranks 3-9: factor rel err {errs.max():.2e}")
+
+
+def test_all_ranks_per_sample_exact_form():
+    _cuda()
+    w = _all_workload()
+    sel = [0, 1, 2, 3, 44, 45, 46, 47]   # samples 0 and 11 at every rank
+    with api.from_workload(w, precision="exact_bf16") as h:
+        _, _, ratio, facs = stepwise_loss_check(w, h, sel, w.sweeps, 1e-8)
+        U = h.get_factors()
+    errs = assert_factors(w, U, facs, sel, 1e-6)
+    print(f"\n'All' exact form: factor rel err {errs.max():.2e}; loss error at most {ratio:.2f} of its bound")
+
+
+def _oracle_stop(w, g, tol, max_sweeps):
+    r = O.jk_als(w.T, w.n_hat, w.left_out, w.init, max_sweeps, tol=tol, blocks=[g])
+    losses = r.losses[:, 0]
+    return r.sweeps_done[0], losses[np.isfinite(losses)][-1], r.normT2[0], r.factors[0]
+
+
+def test_tolerance_run_fp64_stops_each_block_where_the_oracle_does():
+    _cuda()
+    w = W.make_config(1)
+    tol, cap = 1e-6, 1000
+    with api.from_workload(w) as h:
+        done, final = h.run(cap, tol=tol)
+        per = h.run_block_sweeps()
+        st = h.block_status()
+        U = h.get_factors()
+    assert np.all(st & 2), "every block converged"
+    assert done < cap and per.max() <= done
+    sel = [0, 9, 20]
+    for g in sel:
+        n_ora, e_ora, nt, _ = _oracle_stop(w, g, tol, cap)
+        assert per[g] == n_ora, (g, per[g], n_ora)
+        assert abs(final[g] - e_ora) <= 1e-10 * abs(e_ora)
+    ora = O.jk_als(w.T, w.n_hat, w.left_out, w.init, cap, tol=tol, blocks=sel)
+    assert_factors(w, U, ora.factors, sel, 1e-10)
+
+
+def test_tolerance_run_cfg2_exact_form_tol_1e6():
+    """The 300x100x50 workload (300 LOO submodels) at tol 1e-6, at most 1000 sweeps."""
+    _cuda()
+    w = W.make_config(2)
+    tol, cap = 1e-6, 1000
+    with api.from_workload(w, precision="exact_bf16", device="cuda") as h:
+        done, final = h.run(cap, tol=tol)
+        per = h.run_block_sweeps()
+        st = h.block_status()
+    assert np.all(st & 2), "every block converged"
+    assert done <= cap and per.max() <= done
+    for g in (0, 150, 299):
+        n_ora, e_ora, nt, _ = _oracle_stop(w, g, tol, cap)
+        assert abs(int(per[g]) - n_ora) <= 1, (g, per[g], n_ora)
+        # each sweep near the stop changes the loss by less than tol ||T_g||^2 (plus the
+        # form's loss error, far below it)
+        assert abs(final[g] - e_ora) <= 2 * tol * nt, (g, final[g], e_ora)
+    print(f"\ncfg2 exact form, tol {tol:g}: sweeps per block median {int(np.median(per))}, "
+          f"max {per.max()}, run {done}")

@@ -67,3 +67,10 @@ def test_group_blocks_are_contiguous_and_cover_the_mode():
     assert len(b) == 40
     assert np.array_equal(np.concatenate(b), np.arange(400))
     assert all(np.array_equal(D, np.arange(10 * g, 10 * g + 10)) for g, D in enumerate(b))
+
+
+def test_all_ranks_layout_repeats_each_sample_per_rank():
+    """Sec. 5.1 "All": every left-out sample once per rank, ranks cycling within a sample."""
+    blocks, ranks = W.all_ranks_blocks(3, (3, 5))
+    assert [list(b) for b in blocks] == [[0], [0], [1], [1], [2], [2]]
+    assert ranks == [3, 5, 3, 5, 3, 5]
