@@ -100,7 +100,12 @@ typedef struct {
   int autotune;         /* 1: at create, time the MTTKRP (+ split-K reduction) of every mode
                            for split factors around the planned one and keep the fastest
                            (ignored when splits > 0); 0 (default): off                   */
-  int reserved[5];
+  int compact;          /* 1 (default): inside jkcals_run, once at most half of the blocks
+                           being swept are still active, lay the active blocks out side by
+                           side and sweep only them (the MTTKRP then spans only their
+                           columns); the full layout is restored before jkcals_run returns.
+                           0: converged blocks keep their columns until the end           */
+  int reserved[4];
 } jkcals_options;
 
 /* Fill *opt with the defaults above. */

@@ -71,7 +71,8 @@ class JKCALS:
     def __init__(self, T, n_hat: int, ranks: Sequence[int], left_out: Sequence[Sequence[int]],
                  init: Sequence, *, precision: str = "fp64", normalise: bool = True,
                  use_graph: bool = True, splits: int = 0, max_device_bytes: int = 0,
-                 kernel_timing: bool = False, update_mode: int = 0, autotune: bool = False, stream=None):
+                 kernel_timing: bool = False, update_mode: int = 0, autotune: bool = False, compact: bool = True,
+                 stream=None):
         lib = L.load()
         self._lib = lib
         self._h = ct.c_void_p()
@@ -92,6 +93,7 @@ class JKCALS:
         opt.kernel_timing = int(bool(kernel_timing))
         opt.update_mode = int(update_mode)
         opt.autotune = int(bool(autotune))
+        opt.compact = int(bool(compact))
         dims = (ct.c_int64 * self.N)(*self.dims)
         rk = (ct.c_int32 * self.K)(*self.ranks)
         ptr, idx = left_out_csr(left_out)

@@ -154,8 +154,8 @@ void make_plan(jkcals_ctx* h) {
       p.upd.fused = fits ? 1 : 0;
     else if (h->opt.update_mode == 2)
       p.upd.fused = 0;
-    else
-      p.upd.fused = (fits && h->K >= h->num_sms / 2) ? 1 : 0;
+    else   // one CTA per block unless few blocks each carry much FP64 work (large I R^2)
+      p.upd.fused = (fits && (h->K >= h->num_sms / 2 || I * h->Rmax * h->Rmax <= 16384)) ? 1 : 0;
   }
 }
 
@@ -780,6 +780,9 @@ jkcals_status create_impl(jkcals_ctx* h, const void* T, int T_dtype, const int32
     part_bytes = std::max(part_bytes, pb);
     chunks = std::max(chunks, (size_t)h->plan[n].upd.RC * K);
   }
+  // room for the two-phase update of any subset of the blocks (compaction):
+  // RC is at most ceil(2 SMs / K') for K' blocks, so RC K' < 2 SMs + K'
+  chunks = std::max(chunks, (size_t)(2 * h->num_sms + K));
   size_t part_elems = part_bytes / sizeof(double) + 1;
   h->part_bytes = part_elems * sizeof(double);
   JK_TRY(dalloc(h, &h->part, h->part_bytes));
@@ -878,6 +881,7 @@ void jkcals_default_options(jkcals_options* opt) {
   opt->use_graph = 1;
   opt->splits = 0;
   opt->max_device_bytes = 0;
+  opt->compact = 1;
 }
 
 const char* jkcals_last_error(void) { return jk::g_last_error.c_str(); }
@@ -1204,6 +1208,215 @@ jkcals_status jkcals_jackknife_se(jkcals_t h, int ref_block, const double* const
   return JKCALS_OK;
 }
 
+// ---- compaction of converged blocks (jkcals_run) ---------------------------------
+// While compacted, the handle's block arrays (U, Grams, tensor-core factor
+// copies, block metadata, status and losses) hold only the active blocks, side
+// by side; h->cmp keeps the full layout.  Each block's arithmetic does not
+// depend on its position among the columns, so a compacted sweep computes the
+// same per-block update as a full one (the split-K grouping of the sums follows
+// the new plan).
+
+// Fits the current plan into the workspace allocated at create (never
+// reallocated here, so captured graphs, a batch's included, keep valid
+// pointers): a mode whose split-K partials would not fit gets fewer splits, a
+// two-phase update more rows per chunk.
+void fit_plan_to_workspace(jkcals_ctx* h) {
+  const size_t eb = part_kind(h) == kPartF32 ? sizeof(float) : sizeof(double);
+  for (int n = 0; n < h->N; ++n) {
+    while (mode_splits(h, n) > 1 && (size_t)mode_splits(h, n) * h->dims[n] * h->C * eb > h->part_bytes)
+      set_mode_splits(h, n, mode_splits(h, n) / 2);
+    UpdatePlan& u = h->plan[n].upd;
+    if ((size_t)u.RC * h->K > h->upd_chunks) {
+      int64_t RC = std::max<int64_t>(1, (int64_t)(h->upd_chunks / std::max(1, h->K)));
+      const int64_t rpc = (h->dims[n] + RC - 1) / RC;
+      u.rows_per_chunk = (int)rpc;
+      u.RC = (int)((h->dims[n] + rpc - 1) / rpc);
+    }
+  }
+}
+
+// Writes the current (compacted) blocks' state into the full layout of h->cmp.
+jkcals_status compaction_save(jkcals_ctx* h) {
+  jkcals_ctx::Compaction& c = h->cmp;
+  cudaStream_t st = h->stream;
+  std::vector<int> cols(h->C);
+  for (int p = 0; p < h->K; ++p)
+    for (int r = 0; r < h->R[p]; ++r) cols[h->off[p] + r] = c.off[c.cur_to_orig[p]] + r;
+  JK_CUDA(h, cudaMemcpyAsync(c.d_cols, cols.data(), sizeof(int) * h->C, cudaMemcpyHostToDevice, st));
+  for (int n = 0; n < h->N; ++n)
+    JK_CUDA(h, launch_scatter_columns(h->U[n], h->C, c.U[n], c.C, c.d_cols, h->C, h->dims[n], st));
+  std::vector<double> gram(h->gram_total);
+  std::vector<int32_t> status(h->K);
+  std::vector<double> lp(h->K), ll(h->K);
+  for (int n = 0; n < h->N; ++n) {
+    JK_CUDA(h, cudaMemcpyAsync(gram.data(), h->gram[n], sizeof(double) * h->gram_total, cudaMemcpyDeviceToHost, st));
+    JK_CUDA(h, cudaStreamSynchronize(st));
+    for (int p = 0; p < h->K; ++p) {
+      const int a = c.cur_to_orig[p];
+      std::copy(gram.begin() + h->gram_off[p], gram.begin() + h->gram_off[p] + h->R[p] * h->R[p],
+                c.gram[n].begin() + c.gram_off[a]);
+    }
+  }
+  JK_CUDA(h, cudaMemcpyAsync(status.data(), h->d_status, sizeof(int32_t) * h->K, cudaMemcpyDeviceToHost, st));
+  JK_CUDA(h, cudaMemcpyAsync(lp.data(), h->d_loss_prev, sizeof(double) * h->K, cudaMemcpyDeviceToHost, st));
+  JK_CUDA(h, cudaMemcpyAsync(ll.data(), h->d_loss_last, sizeof(double) * h->K, cudaMemcpyDeviceToHost, st));
+  JK_CUDA(h, cudaStreamSynchronize(st));
+  for (int p = 0; p < h->K; ++p) {
+    const int a = c.cur_to_orig[p];
+    c.status[a] = status[p];
+    c.loss_prev[a] = lp[p];
+    c.loss_last[a] = ll[p];
+  }
+  return JKCALS_OK;
+}
+
+// Loads the original blocks `sel` (in this order) from the full layout of
+// h->cmp into the handle's arrays and plans for them.  full: sel is every block
+// and the full layout's plans come back unchanged.
+jkcals_status compaction_load(jkcals_ctx* h, const std::vector<int>& sel, bool full) {
+  jkcals_ctx::Compaction& c = h->cmp;
+  cudaStream_t st = h->stream;
+  const int K = (int)sel.size();
+  h->R.resize(K);
+  h->off.resize(K);
+  h->gram_off.resize(K);
+  h->lo_ptr.assign(1, 0);
+  h->lo_idx.clear();
+  int col = 0, go = 0;
+  h->Rmax = 0;
+  for (int p = 0; p < K; ++p) {
+    const int a = sel[p];
+    h->R[p] = c.R[a];
+    h->off[p] = col;
+    h->gram_off[p] = go;
+    col += c.R[a];
+    go += c.R[a] * c.R[a];
+    h->Rmax = std::max(h->Rmax, c.R[a]);
+    h->lo_idx.insert(h->lo_idx.end(), c.lo_idx.begin() + c.lo_ptr[a], c.lo_idx.begin() + c.lo_ptr[a + 1]);
+    h->lo_ptr.push_back((int64_t)h->lo_idx.size());
+  }
+  h->K = K;
+  h->C = col;
+  h->gram_total = go;
+  h->uniform_rank = true;
+  for (int p = 0; p < K; ++p) h->uniform_rank = h->uniform_rank && h->R[p] == h->Rmax;
+  if (full) {
+    h->Rmax = c.Rmax;
+    h->uniform_rank = c.uniform_rank;
+  }
+  std::vector<int> cols(h->C);
+  for (int p = 0; p < K; ++p)
+    for (int r = 0; r < h->R[p]; ++r) cols[h->off[p] + r] = c.off[sel[p]] + r;
+  std::vector<double> gram(std::max(1, go));
+  std::vector<int32_t> status(K);
+  std::vector<double> nt(K), lp(K), ll(K);
+  for (int p = 0; p < K; ++p) {
+    status[p] = c.status[sel[p]];
+    nt[p] = c.normT2[sel[p]];
+    lp[p] = c.loss_prev[sel[p]];
+    ll[p] = c.loss_last[sel[p]];
+  }
+  JK_CUDA(h, cudaMemcpyAsync(c.d_cols, cols.data(), sizeof(int) * h->C, cudaMemcpyHostToDevice, st));
+  for (int n = 0; n < h->N; ++n)
+    JK_CUDA(h, launch_gather_columns(c.U[n], c.C, h->U[n], h->C, c.d_cols, h->C, h->dims[n], st));
+  for (int n = 0; n < h->N; ++n) {
+    for (int p = 0; p < K; ++p)
+      std::copy(c.gram[n].begin() + c.gram_off[sel[p]], c.gram[n].begin() + c.gram_off[sel[p]] + h->R[p] * h->R[p],
+                gram.begin() + h->gram_off[p]);
+    JK_CUDA(h, cudaMemcpyAsync(h->gram[n], gram.data(), sizeof(double) * go, cudaMemcpyHostToDevice, st));
+    JK_CUDA(h, cudaStreamSynchronize(st));   // gram is reused for the next mode
+  }
+  JK_CUDA(h, cudaMemcpyAsync(h->d_R, h->R.data(), sizeof(int) * K, cudaMemcpyHostToDevice, st));
+  JK_CUDA(h, cudaMemcpyAsync(h->d_off, h->off.data(), sizeof(int) * K, cudaMemcpyHostToDevice, st));
+  JK_CUDA(h, cudaMemcpyAsync(h->d_gram_off, h->gram_off.data(), sizeof(int) * K, cudaMemcpyHostToDevice, st));
+  JK_CUDA(h, cudaMemcpyAsync(h->d_lo_ptr, h->lo_ptr.data(), sizeof(int64_t) * (K + 1), cudaMemcpyHostToDevice, st));
+  if (!h->lo_idx.empty())
+    JK_CUDA(h, cudaMemcpyAsync(h->d_lo_idx, h->lo_idx.data(), sizeof(int64_t) * h->lo_idx.size(),
+                               cudaMemcpyHostToDevice, st));
+  JK_CUDA(h, cudaMemcpyAsync(h->d_status, status.data(), sizeof(int32_t) * K, cudaMemcpyHostToDevice, st));
+  JK_CUDA(h, cudaMemcpyAsync(h->d_normT2, nt.data(), sizeof(double) * K, cudaMemcpyHostToDevice, st));
+  JK_CUDA(h, cudaMemcpyAsync(h->d_loss_prev, lp.data(), sizeof(double) * K, cudaMemcpyHostToDevice, st));
+  JK_CUDA(h, cudaMemcpyAsync(h->d_loss_last, ll.data(), sizeof(double) * K, cudaMemcpyHostToDevice, st));
+  JK_CUDA(h, cudaStreamSynchronize(st));   // the host vectors above are pageable
+  c.cur_to_orig = sel;
+
+  // plans for the new column count; the full layout's plans come back as they were
+  if (full) {
+    for (int n = 0; n < h->N; ++n) {
+      h->plan[n] = c.plan[n];
+      h->tcplan[n] = c.tcplan[n];
+    }
+  } else {
+    if (h->tc) JK_TRY(make_tc_plan(h));
+    make_plan(h);
+    fit_plan_to_workspace(h);
+    size_t fsmem = 0;
+    for (int n = 0; n < h->N; ++n)
+      if (h->plan[n].upd.fused) fsmem = std::max(fsmem, h->plan[n].upd.fused_smem);
+    if (fsmem > 0) JK_CUDA(h, prepare_update_fused(fsmem, h->Rmax, h->uniform_rank));
+  }
+  // the tensor-core forms' transposed FP32 factor copies and column maxima
+  if (h->tc)
+    for (int n = 0; n < h->N; ++n) {
+      JK_CUDA(h, tc::launch_factor_to_ut(h->U[n], h->dims[n], h->C, h->UT[n], h->UTlo[n], h->Ipad[n], st));
+      JK_CUDA(h, tc::launch_colmax(h->UT[n], h->dims[n], h->Ipad[n], h->C, h->cmax[n], st));
+    }
+  h->graph_valid = false;
+  return JKCALS_OK;
+}
+
+// Compacts the handle to the blocks whose status (current positions) is 0.
+jkcals_status compaction_shrink(jkcals_ctx* h, const std::vector<int32_t>& status) {
+  jkcals_ctx::Compaction& c = h->cmp;
+  if (!c.on) {
+    c.K = h->K;
+    c.C = h->C;
+    c.Rmax = h->Rmax;
+    c.gram_total = h->gram_total;
+    c.uniform_rank = h->uniform_rank;
+    c.R = h->R;
+    c.off = h->off;
+    c.gram_off = h->gram_off;
+    c.lo_ptr = h->lo_ptr;
+    c.lo_idx = h->lo_idx;
+    for (int n = 0; n < h->N; ++n) {
+      c.plan[n] = h->plan[n];
+      c.tcplan[n] = h->tcplan[n];
+    }
+    c.status.assign(h->K, 0);
+    c.normT2.assign(h->K, 0.0);
+    c.loss_prev.assign(h->K, 0.0);
+    c.loss_last.assign(h->K, 0.0);
+    JK_CUDA(h, cudaMemcpyAsync(c.normT2.data(), h->d_normT2, sizeof(double) * h->K, cudaMemcpyDeviceToHost,
+                               h->stream));
+    for (int n = 0; n < h->N; ++n) {
+      c.gram[n].assign(std::max(1, h->gram_total), 0.0);
+      if (c.U[n] == nullptr) JK_TRY(dalloc_t(h, &c.U[n], (size_t)h->dims[n] * h->C));
+    }
+    if (c.d_cols == nullptr) JK_TRY(dalloc_t(h, &c.d_cols, (size_t)h->C));
+    c.cur_to_orig.resize(h->K);
+    std::iota(c.cur_to_orig.begin(), c.cur_to_orig.end(), 0);
+    c.on = true;
+  }
+  JK_TRY(compaction_save(h));
+  std::vector<int> sel;
+  for (int p = 0; p < h->K; ++p)
+    if (status[p] == 0) sel.push_back(c.cur_to_orig[p]);
+  return compaction_load(h, sel, false);
+}
+
+// Restores the full layout (every block in its original place).
+jkcals_status compaction_restore(jkcals_ctx* h) {
+  jkcals_ctx::Compaction& c = h->cmp;
+  if (!c.on) return JKCALS_OK;
+  JK_TRY(compaction_save(h));
+  std::vector<int> all(c.K);
+  std::iota(all.begin(), all.end(), 0);
+  JK_TRY(compaction_load(h, all, true));
+  c.on = false;
+  return JKCALS_OK;
+}
+
 jkcals_status jkcals_run(jkcals_t h, int max_sweeps, double tol, int* sweeps_done, double* final_loss) {
   JK_TRY(check_handle(h));
   if (max_sweeps < 0 || !(tol >= 0.0)) return fail(JKCALS_ERR_ARG, "bad max_sweeps or tol");
@@ -1212,26 +1425,42 @@ jkcals_status jkcals_run(jkcals_t h, int max_sweeps, double tol, int* sweeps_don
   h->tol_host = tol;
   JK_CUDA(h, cudaMemcpyAsync(h->d_tol, &h->tol_host, sizeof(double), cudaMemcpyHostToDevice, h->stream));
   int done = 0;
-  std::vector<int32_t> st(h->K);
-  std::vector<double> lh((size_t)chunk * h->K);
+  std::vector<int32_t> st;
+  std::vector<double> lh;
   h->run_block_sweeps.assign(h->K, 0);
-  while (done < max_sweeps) {
+  // one chunk of sweeps, the per-block bookkeeping, and the compaction once at
+  // most half of the blocks being swept are still active
+  auto chunk_step = [&](bool& stop) -> jkcals_status {
     const int n = std::min(chunk, max_sweeps - done);
     JK_CUDA(h, cudaMemsetAsync(h->d_sweep_idx, 0, sizeof(int), h->stream));
     JK_TRY(run_sweeps(h, n));
     done += n;
+    st.resize(h->K);
+    lh.resize((size_t)n * h->K);
     JK_CUDA(h, cudaMemcpyAsync(st.data(), h->d_status, sizeof(int32_t) * h->K, cudaMemcpyDeviceToHost, h->stream));
     // a block's loss is NaN in the sweeps after it froze: its sweeps are the finite ones
     JK_CUDA(h, cudaMemcpyAsync(lh.data(), h->loss_hist, sizeof(double) * n * h->K, cudaMemcpyDeviceToHost,
                                h->stream));
     JK_CUDA(h, cudaStreamSynchronize(h->stream));
     for (int t = 0; t < n; ++t)
-      for (int g = 0; g < h->K; ++g)
-        if (std::isfinite(lh[(size_t)t * h->K + g])) ++h->run_block_sweeps[g];
-    bool all_frozen = true;
-    for (int32_t v : st) all_frozen = all_frozen && (v != 0);
-    if (all_frozen) break;
-  }
+      for (int p = 0; p < h->K; ++p)
+        if (std::isfinite(lh[(size_t)t * h->K + p])) ++h->run_block_sweeps[h->cmp.on ? h->cmp.cur_to_orig[p] : p];
+    int active = 0;
+    for (int32_t v : st) active += v == 0 ? 1 : 0;
+    if (active == 0 || done >= max_sweeps) {
+      stop = true;
+      return JKCALS_OK;
+    }
+    if (h->opt.compact && 2 * active <= h->K) JK_TRY(compaction_shrink(h, st));
+    return JKCALS_OK;
+  };
+  jkcals_status rs = JKCALS_OK;
+  bool stop = max_sweeps == 0;
+  while (!stop && rs == JKCALS_OK) rs = chunk_step(stop);
+  // every block back in its original place, also after a failure
+  const jkcals_status rr = compaction_restore(h);
+  if (rs != JKCALS_OK) return rs;
+  JK_TRY(rr);
   h->tol_host = 0.0;
   JK_CUDA(h, cudaMemsetAsync(h->d_tol, 0, sizeof(double), h->stream));
   if (sweeps_done) *sweeps_done = done;

@@ -180,6 +180,25 @@ struct jkcals_ctx {
   int* d_err = nullptr;                      // bounded-wait expiry code of the TC kernel
   std::vector<int32_t> run_block_sweeps;     // sweeps each block ran in the latest jkcals_run
 
+  // compaction of converged blocks inside jkcals_run: while compacted, the
+  // handle's block arrays hold only the active blocks (block p is the original
+  // block cur_to_orig[p]); the full layout is kept here and restored at the end
+  struct Compaction {
+    bool on = false;
+    std::vector<int> cur_to_orig;
+    int K = 0, C = 0, Rmax = 0, gram_total = 0;
+    bool uniform_rank = true;
+    std::vector<int> R, off, gram_off;
+    std::vector<int64_t> lo_ptr, lo_idx;
+    std::vector<int32_t> status;
+    std::vector<double> normT2, loss_prev, loss_last;
+    std::vector<double> gram[jk::kMaxModes];   // host copies of the packed Grams
+    double* U[jk::kMaxModes] = {nullptr};      // device, full I_n x C layout
+    int* d_cols = nullptr;                     // device column map (C ints)
+    jk::ModePlan plan[jk::kMaxModes];          // the full layout's plans, restored as they were
+    jk::tc::TcPlan tcplan[jk::kMaxModes];
+  } cmp;
+
   cudaGraphExec_t sweep_exec = nullptr;
   bool graph_valid = false;
 
@@ -256,6 +275,11 @@ cudaError_t launch_block_norms(const double* slice, int64_t I, int K, BlockMeta 
                                cudaStream_t s);
 // Zero rows D_g of block g of the sampled mode's multi-matrix.
 cudaError_t launch_zero_left_out(double* U, int C, int K, BlockMeta bm, cudaStream_t s);
+// column moves between row-major matrices (compaction of converged blocks, jk_capi.cu)
+cudaError_t launch_gather_columns(const double* src, int64_t ld_src, double* dst, int64_t ld_dst, const int* src_col,
+                                  int ncols, int64_t rows, cudaStream_t s);
+cudaError_t launch_scatter_columns(const double* src, int64_t ld_src, double* dst, int64_t ld_dst, const int* dst_col,
+                                   int ncols, int64_t rows, cudaStream_t s);
 // G^(n)_g for every block of one mode.
 cudaError_t launch_grams(const double* U, int64_t I, int C, int K, BlockMeta bm, double* gram,
                          cudaStream_t s);

@@ -148,4 +148,48 @@ cudaError_t launch_grams(const double* U, int64_t I, int C, int K, BlockMeta bm,
   return cudaGetLastError();
 }
 
+namespace {
+// Column moves between two row-major matrices of `rows` rows: gather takes
+// column src_col[j] of src into column j of dst; scatter puts column j of src
+// into column dst_col[j] of dst.
+__global__ void gather_columns_kernel(const double* __restrict__ src, int64_t ld_src, double* __restrict__ dst,
+                                      int64_t ld_dst, const int* __restrict__ src_col, int ncols, int64_t rows) {
+  const int64_t total = rows * ncols;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / ncols;
+    const int j = (int)(e - i * ncols);
+    dst[i * ld_dst + j] = src[i * ld_src + src_col[j]];
+  }
+}
+
+__global__ void scatter_columns_kernel(const double* __restrict__ src, int64_t ld_src, double* __restrict__ dst,
+                                       int64_t ld_dst, const int* __restrict__ dst_col, int ncols, int64_t rows) {
+  const int64_t total = rows * ncols;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / ncols;
+    const int j = (int)(e - i * ncols);
+    dst[i * ld_dst + dst_col[j]] = src[i * ld_src + j];
+  }
+}
+
+unsigned col_blocks(int64_t total) {
+  int64_t b = (total + 255) / 256;
+  return (unsigned)(b < 1 ? 1 : (b > 4096 ? 4096 : b));
+}
+}  // namespace
+
+cudaError_t launch_gather_columns(const double* src, int64_t ld_src, double* dst, int64_t ld_dst, const int* src_col,
+                                  int ncols, int64_t rows, cudaStream_t s) {
+  if (ncols <= 0 || rows <= 0) return cudaSuccess;
+  gather_columns_kernel<<<col_blocks(rows * ncols), 256, 0, s>>>(src, ld_src, dst, ld_dst, src_col, ncols, rows);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scatter_columns(const double* src, int64_t ld_src, double* dst, int64_t ld_dst, const int* dst_col,
+                                   int ncols, int64_t rows, cudaStream_t s) {
+  if (ncols <= 0 || rows <= 0) return cudaSuccess;
+  scatter_columns_kernel<<<col_blocks(rows * ncols), 256, 0, s>>>(src, ld_src, dst, ld_dst, dst_col, ncols, rows);
+  return cudaGetLastError();
+}
+
 }  // namespace jk

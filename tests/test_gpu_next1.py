@@ -108,3 +108,40 @@ def test_tolerance_run_cfg2_exact_form_tol_1e6():
         assert abs(final[g] - e_ora) <= 2 * tol * nt, (g, final[g], e_ora)
     print(f"\ncfg2 exact form, tol {tol:g}: sweeps per block median {int(np.median(per))}, "
           f"max {per.max()}, run {done}")
+
+
+@pytest.mark.parametrize("precision,bar", [("fp64", 1e-10), ("exact_bf16", 1e-6)])
+def test_compaction_of_converged_blocks_matches_the_full_layout(precision, bar):
+    """jkcals_run lays the still-active blocks out side by side once at most half
+    of them are active, and restores the full layout before returning.  Every
+    block must stop at the same sweep as in a run without compaction, with the
+    same status and (within the form's bar: the split-K grouping of the sums
+    follows the smaller plan) the same factors and final loss.  Mixed ranks 3-9
+    ("All" layout), so the compacted layouts are not uniform and the two-phase
+    update runs once few blocks remain."""
+    _cuda()
+    w = _all_workload()
+    tol, cap = 1e-7, 400
+    res = {}
+    for compact in (True, False):
+        with api.from_workload(w, precision=precision, compact=compact) as h:
+            done, final = h.run(cap, tol=tol)
+            res[compact] = (done, final, h.run_block_sweeps(), h.block_status(), h.get_factors(), h.K, h.C)
+            # the handle is back in its full layout and keeps working after the run
+            assert h.als_sweep(1).shape == (1, w.K)
+    (d1, f1, p1, s1, U1, K1, C1), (d0, f0, p0, s0, U0, K0, C0) = res[True], res[False]
+    assert (K1, C1) == (K0, C0) == (w.K, w.C)
+    np.testing.assert_array_equal(p1, p0)
+    np.testing.assert_array_equal(s1, s0)
+    assert d1 == d0
+    assert p1.min() < p1.max(), "blocks converge at different sweeps, so compaction happened"
+    np.testing.assert_allclose(f1, f0, rtol=bar)
+    for a, b in zip(U1, U0):
+        np.testing.assert_allclose(a, b, rtol=bar, atol=bar * np.abs(b).max())
+    # and the compacted run against the oracle's own stopping rule on sampled blocks
+    for g in (0, 7, 45):
+        n_ora, e_ora, nt, facs = _oracle_stop(w, g, tol, cap)
+        assert abs(int(p1[g]) - n_ora) <= (0 if precision == "fp64" else 1), (g, p1[g], n_ora)
+        if precision == "fp64":
+            assert abs(f1[g] - e_ora) <= 1e-10 * abs(e_ora)
+            assert_factors(w, U1, [facs], [g], 1e-10)
