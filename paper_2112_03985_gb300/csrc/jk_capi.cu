@@ -162,7 +162,9 @@ void make_plan(jkcals_ctx* h) {
 int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 
 // Tensor-core plan of every mode: N tile, split-K factor, pipeline depths.
-constexpr size_t kSmemOptin = 227 * 1024;   // dynamic shared memory per CTA (opt-in limit)
+// dynamic shared memory per CTA (opt-in limit 227 KB, less 512 bytes for the
+// arguments that a grouped launch keeps in static shared memory)
+constexpr size_t kSmemOptin = 227 * 1024 - 512;
 
 jkcals_status make_tc_plan(jkcals_ctx* h) {
   const int prec = h->opt.precision;
@@ -345,6 +347,9 @@ UpdateArgs update_args(jkcals_ctx* h, int n, const void* part, int part_kind, in
   return a;
 }
 
+tc::TcArgs make_tc_args(jkcals_ctx* h, int n, float* const* UT, float* const* UTlo, float* const* cmax,
+                        bool reuse_slices);
+
 // Enqueue the concurrent MTTKRP of mode n for factor set (U, UT, cmax) into h->part.
 // reuse_slices: a two-step mode may reuse the U_a slices left in At by the
 // previous two-step launch of the same sweep when mode a was not updated since.
@@ -357,6 +362,14 @@ jkcals_status enqueue_mttkrp(jkcals_ctx* h, int n, double* const* U, float* cons
                                  static_cast<double*>(h->part), h->stream));
     return JKCALS_OK;
   }
+  const tc::TcArgs a = make_tc_args(h, n, UT, UTlo, cmax, reuse_slices);
+  JK_CUDA(h, tc::launch_mttkrp_tc(h->opt.precision, h->tcplan[n], a, h->stream));
+  return JKCALS_OK;
+}
+
+// Arguments of mode n's tensor-core MTTKRP for factor copies (UT, UTlo, cmax).
+tc::TcArgs make_tc_args(jkcals_ctx* h, int n, float* const* UT, float* const* UTlo, float* const* cmax,
+                        bool reuse_slices) {
   const tc::TcPlan& p = h->tcplan[n];
   tc::TcArgs a{};
   a.I = h->dims[n];
@@ -401,8 +414,9 @@ jkcals_status enqueue_mttkrp(jkcals_ctx* h, int n, double* const* U, float* cons
   a.Ia = (int)h->dims[p.a_mode];
   a.ut_stride_a = h->Ipad[p.a_mode];
   a.skip_slice = (p.tts && reuse_slices) ? 1 : 0;
-  JK_CUDA(h, tc::launch_mttkrp_tc(h->opt.precision, p, a, h->stream));
-  return JKCALS_OK;
+  a.tiles_c = p.tiles_c;
+  a.tiles_n = p.tiles_n;
+  return a;
 }
 
 int mode_splits(const jkcals_ctx* h, int n) { return h->tc ? h->tcplan[n].splits : h->plan[n].splits; }
@@ -1529,6 +1543,8 @@ jkcals_status jkcals_sync(jkcals_t h) {
 }
 
 
+}  // extern "C"
+
 struct jkcals_batch_ctx {
   std::vector<jkcals_ctx*> hs;
   std::vector<double*> loss_ptrs;   // each handle's loss history when the graph was captured
@@ -1538,12 +1554,216 @@ struct jkcals_batch_ctx {
   bool owns_stream = false;
   cudaGraphExec_t exec = nullptr;
   int max_sweeps = 0;
+  bool grouped = false;             // one launch per kernel step for all problems
+  std::vector<void*> dev;           // device tables of the grouped launches
 };
+
+namespace {
+
+// A batch sweep runs as grouped launches when every problem uses the same
+// tensor-core form and order and no mode takes the two-step form.
+bool batch_groupable(const std::vector<jkcals_ctx*>& hs) {
+  for (jkcals_ctx* h : hs) {
+    if (!h->tc || h->opt.precision != hs[0]->opt.precision || h->N != hs[0]->N) return false;
+    for (int n = 0; n < h->N; ++n)
+      if (h->tcplan[n].tts) return false;
+  }
+  return true;
+}
+
+jkcals_status batch_upload(jkcals_batch_ctx* b, void** dst, const void* src, size_t bytes) {
+  cudaError_t e = cudaMalloc(dst, bytes);
+  if (e != cudaSuccess) return fail(JKCALS_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  b->dev.push_back(*dst);
+  e = cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return fail(JKCALS_ERR_CUDA, std::string("cudaMemcpy: ") + cudaGetErrorString(e));
+  return JKCALS_OK;
+}
+
+// One grouped MTTKRP of mode n over all problems, from their current plans.
+struct GroupedMttkrp {
+  const tc::TcArgs* args = nullptr;
+  const int* first = nullptr;
+  int total = 0;
+  bool qm_small = true;
+  size_t smem = 0;
+};
+
+jkcals_status build_grouped_mttkrp(jkcals_batch_ctx* b, int n, GroupedMttkrp& g) {
+  const int P = (int)b->hs.size();
+  std::vector<tc::TcArgs> args(P);
+  std::vector<int> first(P + 1, 0);
+  g = GroupedMttkrp{};
+  for (int i = 0; i < P; ++i) {
+    jkcals_ctx* h = b->hs[i];
+    const tc::TcPlan& p = h->tcplan[n];
+    args[i] = make_tc_args(h, n, h->UT, h->UTlo, h->cmax, false);
+    first[i + 1] = first[i] + p.tiles_c * p.tiles_n * p.splits;
+    g.qm_small = g.qm_small && args[i].nq <= 2;
+    g.smem = std::max(g.smem, tc::tc_smem_bytes(p));
+  }
+  g.total = first[P];
+  void* da = nullptr;
+  void* df = nullptr;
+  JK_TRY(batch_upload(b, &da, args.data(), sizeof(tc::TcArgs) * P));
+  JK_TRY(batch_upload(b, &df, first.data(), sizeof(int) * (P + 1)));
+  g.args = static_cast<const tc::TcArgs*>(da);
+  g.first = static_cast<const int*>(df);
+  const cudaError_t e = tc::prepare_mttkrp_tc_grouped(b->hs[0]->opt.precision, g.qm_small, g.smem);
+  if (e != cudaSuccess) return fail(JKCALS_ERR_CUDA, std::string("grouped MTTKRP attributes: ") + cudaGetErrorString(e));
+  return JKCALS_OK;
+}
+
+jkcals_status launch_grouped_mttkrp(jkcals_batch_ctx* b, const GroupedMttkrp& g) {
+  const cudaError_t e = tc::launch_mttkrp_tc_grouped(b->hs[0]->opt.precision, g.args, g.first, (int)b->hs.size(),
+                                                     g.total, g.qm_small, g.smem, b->stream);
+  if (e != cudaSuccess) return fail(JKCALS_ERR_CUDA, std::string("grouped MTTKRP: ") + cudaGetErrorString(e));
+  return JKCALS_OK;
+}
+
+// Batch autotuner (any handle created with opt.autotune): per mode, the split
+// factor of every problem scaled by 1, 1/2, 1/4 or 1/8 (a CTA's share of the
+// contraction grows as the problems share the GPU), the fastest grouped MTTKRP
+// kept (one warm-up and three timed launches each, CUDA events on the batch's
+// stream; the launches write only the split-K partials).
+jkcals_status autotune_grouped(jkcals_batch_ctx* b) {
+  const int P = (int)b->hs.size();
+  const int N = b->hs[0]->N;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+    return fail(JKCALS_ERR_CUDA, "cudaEventCreate");
+  jkcals_status st = JKCALS_OK;
+  for (int n = 0; n < N && st == JKCALS_OK; ++n) {
+    std::vector<int> base(P);
+    for (int i = 0; i < P; ++i) base[i] = mode_splits(b->hs[i], n);
+    int best_scale = 1;
+    float best_ms = 1e30f;
+    for (int scale = 1; scale <= 8 && st == JKCALS_OK; scale *= 2) {
+      for (int i = 0; i < P; ++i) set_mode_splits(b->hs[i], n, std::max(1, base[i] / scale));
+      GroupedMttkrp g;
+      st = build_grouped_mttkrp(b, n, g);
+      float tot = 0.f;
+      for (int r = 0; r < 4 && st == JKCALS_OK; ++r) {
+        cudaEventRecord(e0, b->stream);
+        st = launch_grouped_mttkrp(b, g);
+        cudaEventRecord(e1, b->stream);
+        if (cudaEventSynchronize(e1) != cudaSuccess) st = fail(JKCALS_ERR_CUDA, "grouped MTTKRP timing");
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (r > 0) tot += ms;
+      }
+      if (st == JKCALS_OK && tot < best_ms) {
+        best_ms = tot;
+        best_scale = scale;
+      }
+    }
+    for (int i = 0; i < P; ++i) set_mode_splits(b->hs[i], n, std::max(1, base[i] / best_scale));
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return st;
+}
+
+// Captures one grouped sweep of every problem on the batch's stream: per mode,
+// one MTTKRP launch for all problems, one fused-update launch per rank class
+// (each problem's block arithmetic is that of its own sweep), the other
+// problems' split-K reduction and two-phase update, then every sweep counter.
+jkcals_status capture_grouped(jkcals_batch_ctx* b, cudaGraph_t* graph) {
+  const int P = (int)b->hs.size();
+  const int N = b->hs[0]->N;
+  std::vector<GroupedMttkrp> mt(N);
+  struct UpdClass {
+    int Rmax;
+    bool uniform;
+    int threads = 0;
+    size_t smem = 0;
+    std::vector<UpdateArgs> args;
+    std::vector<int> first{0};
+    const UpdateArgs* dargs = nullptr;
+    const int* dfirst = nullptr;
+  };
+  std::vector<std::vector<UpdClass>> upd(N);
+  for (int n = 0; n < N; ++n) {
+    JK_TRY(build_grouped_mttkrp(b, n, mt[n]));
+    for (jkcals_ctx* h : b->hs) {
+      if (!h->plan[n].upd.fused) continue;
+      UpdClass* c = nullptr;
+      for (UpdClass& u : upd[n])
+        if (u.Rmax == h->Rmax && u.uniform == h->uniform_rank) c = &u;
+      if (c == nullptr) {
+        upd[n].push_back(UpdClass{h->Rmax, h->uniform_rank});
+        c = &upd[n].back();
+      }
+      c->args.push_back(update_args(h, n, h->part, part_kind(h), mode_splits(h, n)));
+      c->first.push_back(c->first.back() + h->K);
+      c->threads = std::max(c->threads, update_fused_threads(h->dims[n], h->Rmax, h->uniform_rank));
+      c->smem = std::max(c->smem, h->plan[n].upd.fused_smem);
+    }
+    for (UpdClass& c : upd[n]) {
+      void* da = nullptr;
+      void* df = nullptr;
+      JK_TRY(batch_upload(b, &da, c.args.data(), sizeof(UpdateArgs) * c.args.size()));
+      JK_TRY(batch_upload(b, &df, c.first.data(), sizeof(int) * c.first.size()));
+      c.dargs = static_cast<const UpdateArgs*>(da);
+      c.dfirst = static_cast<const int*>(df);
+      const cudaError_t e = prepare_update_grouped(c.threads, c.Rmax, c.uniform, c.smem);
+      if (e != cudaSuccess) return fail(JKCALS_ERR_CUDA, std::string("grouped update attributes: ") + cudaGetErrorString(e));
+    }
+  }
+  std::vector<int*> counters(P);
+  for (int i = 0; i < P; ++i) counters[i] = b->hs[i]->d_sweep_idx;
+  void* dc = nullptr;
+  JK_TRY(batch_upload(b, &dc, counters.data(), sizeof(int*) * P));
+
+  cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return fail(JKCALS_ERR_CUDA, std::string("cudaStreamBeginCapture: ") + cudaGetErrorString(e));
+  jkcals_status st = JKCALS_OK;
+  for (int n = 0; n < N && st == JKCALS_OK; ++n) {
+    st = launch_grouped_mttkrp(b, mt[n]);
+    for (const UpdClass& c : upd[n]) {
+      if (st != JKCALS_OK) break;
+      e = launch_update_grouped(c.dargs, c.dfirst, (int)c.args.size(), c.first.back(), c.threads, c.Rmax, c.uniform,
+                                c.smem, b->stream);
+      if (e != cudaSuccess)
+        st = fail(JKCALS_ERR_CUDA, std::string("grouped update (mode ") + std::to_string(n) + ", rank class " +
+                                       std::to_string(c.Rmax) + (c.uniform ? " uniform" : " mixed") + ", " +
+                                       std::to_string(c.threads) + " threads, " + std::to_string(c.smem) +
+                                       " B dynamic shared memory, " + std::to_string(c.first.back()) +
+                                       " blocks; " + grouped_update_attrs() + "): " + cudaGetErrorString(e));
+    }
+    for (jkcals_ctx* h : b->hs) {
+      if (st != JKCALS_OK || h->plan[n].upd.fused) continue;
+      const int64_t cnt = h->dims[n] * (int64_t)h->C;
+      e = part_kind(h) == kPartF32x2
+              ? launch_reduce_partials_f32x2(static_cast<float2*>(h->part), mode_splits(h, n), cnt, h->mbuf, b->stream)
+              : launch_reduce_partials_f32(static_cast<float*>(h->part), mode_splits(h, n), cnt, h->mbuf, b->stream);
+      if (e == cudaSuccess) e = launch_update(update_args(h, n, h->mbuf, kPartF64, 1), b->stream);
+      if (e != cudaSuccess) st = fail(JKCALS_ERR_CUDA, std::string("batched two-phase update: ") + cudaGetErrorString(e));
+    }
+  }
+  if (st == JKCALS_OK) {
+    e = launch_advance_sweeps(static_cast<int* const*>(dc), P, b->stream);
+    if (e != cudaSuccess) st = fail(JKCALS_ERR_CUDA, std::string("sweep counters: ") + cudaGetErrorString(e));
+  }
+  e = cudaStreamEndCapture(b->stream, graph);
+  if (st != JKCALS_OK) {
+    if (*graph) cudaGraphDestroy(*graph);
+    *graph = nullptr;
+    return st;
+  }
+  if (e != cudaSuccess) return fail(JKCALS_ERR_CUDA, std::string("cudaStreamEndCapture: ") + cudaGetErrorString(e));
+  return JKCALS_OK;
+}
+
+}  // namespace
+
+extern "C" {
 
 void jkcals_batch_destroy(jkcals_batch_t b) {
   if (b == nullptr) return;
   if (b->stream) cudaStreamSynchronize(b->stream);
   if (b->exec) cudaGraphExecDestroy(b->exec);
+  for (void* p : b->dev) cudaFree(p);
   for (cudaEvent_t e : b->ready)
     if (e) cudaEventDestroy(e);
   if (b->done) cudaEventDestroy(b->done);
@@ -1578,6 +1798,39 @@ jkcals_status jkcals_batch_create(jkcals_batch_t* out, int n, const jkcals_t* ha
   }
   if ((e = cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming)) != cudaSuccess)
     return bail(fail(JKCALS_ERR_CUDA, std::string("cudaEventCreate: ") + cudaGetErrorString(e)));
+  std::vector<jkcals_ctx*> hv(handles, handles + n);
+  if (batch_groupable(hv)) {
+    // one launch per kernel step for all problems (see capture_grouped)
+    b->grouped = true;
+    for (int i = 0; i < n; ++i) {
+      jkcals_ctx* h = handles[i];
+      jkcals_status s = ensure_loss_cap(h, max_sweeps);
+      if (s != JKCALS_OK) return bail(s);
+      cudaEvent_t ev = nullptr;
+      if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess)
+        return bail(fail(JKCALS_ERR_CUDA, std::string("cudaEventCreate: ") + cudaGetErrorString(e)));
+      b->ready.push_back(ev);
+      if ((e = cudaStreamSynchronize(h->stream)) != cudaSuccess)
+        return bail(fail(JKCALS_ERR_CUDA, std::string("cudaStreamSynchronize: ") + cudaGetErrorString(e)));
+      b->hs.push_back(h);
+      b->loss_ptrs.push_back(h->loss_hist);
+    }
+    bool tune = false;
+    for (jkcals_ctx* h : b->hs) tune = tune || (h->opt.autotune && h->opt.splits <= 0);
+    if (tune) {
+      const jkcals_status s = autotune_grouped(b);
+      if (s != JKCALS_OK) return bail(s);
+    }
+    cudaGraph_t gg = nullptr;
+    const jkcals_status s = capture_grouped(b, &gg);
+    if (s != JKCALS_OK) return bail(s);
+    e = cudaGraphInstantiate(&b->exec, gg, 0);
+    cudaGraphDestroy(gg);
+    if (e != cudaSuccess)
+      return bail(fail(JKCALS_ERR_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e)));
+    *out = b;
+    return JKCALS_OK;
+  }
   cudaGraph_t g = nullptr;
   if ((e = cudaGraphCreate(&g, 0)) != cudaSuccess)
     return bail(fail(JKCALS_ERR_CUDA, std::string("cudaGraphCreate: ") + cudaGetErrorString(e)));

@@ -332,8 +332,20 @@ cudaError_t launch_update(const UpdateArgs& a, cudaStream_t s);
 size_t update_fused_smem(int64_t I, int Rmax);
 cudaError_t prepare_update_fused(size_t smem, int Rmax, bool uniform_rank);
 cudaError_t launch_update_fused(const UpdateArgs& a, size_t smem, int Rmax, bool uniform_rank, cudaStream_t s);
+// The fused updates of several problems of one rank class (Rmax, uniform) in one
+// launch: args[b] (device) is problem b's UpdateArgs, first[b] its first block
+// (nprob + 1 entries); threads: the largest update_fused_threads of the
+// problems (a CTA's surplus threads take no rows); smem: the largest
+// update_fused_smem.  Each block's arithmetic is that of launch_update_fused
+// for its problem.
+int update_fused_threads(int64_t I, int Rmax, bool uniform);
+std::string grouped_update_attrs();   // diagnostics of the last grouped update launch
+cudaError_t prepare_update_grouped(int threads, int Rmax, bool uniform, size_t smem);
+cudaError_t launch_update_grouped(const UpdateArgs* args, const int* first, int nprob, int total, int threads,
+                                  int Rmax, bool uniform, size_t smem, cudaStream_t s);
 
 cudaError_t launch_advance_sweep(int* sweep_idx, cudaStream_t s);
+cudaError_t launch_advance_sweeps(int* const* sweep_idx, int n, cudaStream_t s);   // n device counters
 
 // ---- gradient epilogue (jk_update.cu) ----------------------------------------
 // G_n(i, c) = 2 (U_n H_n - M_n)(i, c) per block, rows D_g of the sampled mode set to 0.

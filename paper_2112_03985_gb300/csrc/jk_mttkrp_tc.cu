@@ -295,11 +295,10 @@ __device__ __forceinline__ void issue_stage(uint32_t tmem, uint64_t ad0, uint64_
 // QM: slots for the remaining modes beyond a that the producers track (the
 // column index carry, the factor entries of Q) — 2 covers tensors of up to 4
 // modes with short per-k-step index code, kMaxModes - 2 the rest.
+// The CTA (bx, by, bz) of one problem's launch: C tile bx, N tile by, split bz.
+// smem: the 1024-byte aligned dynamic shared memory.
 template <class Cfg, int QM>
-__global__ void __launch_bounds__(kThreads, 1) mttkrp_tc_kernel(const TcArgs a) {
-  extern __shared__ __align__(1024) unsigned char smem_raw[];
-  unsigned char* smem =
-      reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+__device__ __forceinline__ void mttkrp_tc_body(const TcArgs& a, int bx, int by, int bz, unsigned char* smem) {
   constexpr int NS = Cfg::nsplit;
   constexpr int ROW = Cfg::row_bytes;            // bytes of K per operand row in one stage
   constexpr int BK = ROW / Cfg::elem;            // columns of T_(n) per stage
@@ -332,9 +331,9 @@ __global__ void __launch_bounds__(kThreads, 1) mttkrp_tc_kernel(const TcArgs a) 
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   int* srowexp = const_cast<int*>(abort_flag + 1);   // BN row exponents of this N tile (exact form)
 
-  const int c0 = blockIdx.x * kRowsM;
-  const int n0 = blockIdx.y * a.BN;
-  const int64_t jb = (int64_t)blockIdx.z * a.kchunk;
+  const int c0 = bx * kRowsM;
+  const int n0 = by * a.BN;
+  const int64_t jb = (int64_t)bz * a.kchunk;
   int64_t je = jb + a.kchunk;
   if (je > a.Jp) je = a.Jp;
   const int nk = (je > jb) ? (int)((je - jb + BK - 1) / BK) : 0;
@@ -378,8 +377,8 @@ __global__ void __launch_bounds__(kThreads, 1) mttkrp_tc_kernel(const TcArgs a) 
     // the S stages are issued by S lanes.
     if (lane < S) {
       int issued = 0;
-      // this CTA's first stage image: N tile blockIdx.y, k-step jb / BK
-      const unsigned char* src = a.Tt + ((int64_t)blockIdx.y * a.nkt + jb / BK) * (int64_t)b_stage;
+      // this CTA's first stage image: N tile by, k-step jb / BK
+      const unsigned char* src = a.Tt + ((int64_t)by * a.nkt + jb / BK) * (int64_t)b_stage;
       unsigned char* dst = ring + (size_t)lane * stage_bytes + a_stage;
       uint32_t ph = 0;   // parity of this stage's pass
       for (int it = lane; it < nk; it += S, ph ^= 1u) {
@@ -487,7 +486,7 @@ __global__ void __launch_bounds__(kThreads, 1) mttkrp_tc_kernel(const TcArgs a) 
           if (a.nlev > 1) tmem_ld16(col + L, v1);
           if (a.nlev > 2) tmem_ld16(col + 2 * L, v2);
           tmem_ld_wait();
-          float* out = a.part + (int64_t)blockIdx.z * a.I * a.C;
+          float* out = a.part + (int64_t)bz * a.I * a.C;
 #pragma unroll
           for (int r = 0; r < 16; ++r) {
             const int64_t i = (int64_t)n0 + cc + r;
@@ -508,7 +507,7 @@ __global__ void __launch_bounds__(kThreads, 1) mttkrp_tc_kernel(const TcArgs a) 
           // levels 0 and 1 are exact; add the levels as an unevaluated FP32 pair
           // (hi, lo) with error-free TwoSum steps, scale by 2^(E_c + F_i - 14)
           // and add the pair into the partial; the consumer adds hi + lo
-          float2* out2 = reinterpret_cast<float2*>(a.part) + (int64_t)blockIdx.z * a.I * a.C;
+          float2* out2 = reinterpret_cast<float2*>(a.part) + (int64_t)bz * a.I * a.C;
 #pragma unroll
           for (int r = 0; r < 16; ++r) {
             const int64_t i = (int64_t)n0 + cc + r;
@@ -891,6 +890,46 @@ __global__ void __launch_bounds__(kThreads, 1) mttkrp_tc_kernel(const TcArgs a) 
     tc_fence_after();
     tmem_dealloc(tmem, (uint32_t)a.tmem_cols);
   }
+}
+
+template <class Cfg, int QM>
+__global__ void __launch_bounds__(kThreads, 1) mttkrp_tc_kernel(const TcArgs a) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* smem =
+      reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  mttkrp_tc_body<Cfg, QM>(a, blockIdx.x, blockIdx.y, blockIdx.z, smem);
+}
+
+// Several problems' MTTKRPs of one mode in one launch: CTA x belongs to the
+// problem b with first[b] <= x < first[b + 1] and is CTA (x - first[b]) of that
+// problem's own grid (C tiles fastest, then N tiles, then splits).  The
+// problem's arguments are copied into shared memory once per CTA.
+__device__ __forceinline__ int group_problem(const int* first, int nprob, int x) {
+  int lo = 0, hi = nprob - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (__ldg(first + mid) <= x) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+template <class Cfg, int QM>
+__global__ void __launch_bounds__(kThreads, 1) mttkrp_tc_grouped_kernel(const TcArgs* __restrict__ args,
+                                                                        const int* __restrict__ first, int nprob) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  __shared__ __align__(16) TcArgs sa;
+  unsigned char* smem =
+      reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const int b = group_problem(first, nprob, (int)blockIdx.x);
+  {
+    const uint32_t* src = reinterpret_cast<const uint32_t*>(args + b);
+    uint32_t* dst = reinterpret_cast<uint32_t*>(&sa);
+    for (int i = threadIdx.x; i < (int)(sizeof(TcArgs) / 4); i += blockDim.x) dst[i] = __ldg(src + i);
+  }
+  __syncthreads();
+  const int local = (int)blockIdx.x - __ldg(first + b);
+  const int gx = sa.tiles_c, gy = sa.tiles_n;
+  mttkrp_tc_body<Cfg, QM>(sa, local % gx, (local / gx) % gy, local / (gx * gy), smem);
 }
 
 // ---- precision forms -----------------------------------------------------------
@@ -1332,7 +1371,47 @@ cudaError_t launch_cfg(const TcPlan& p, const TcArgs& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+template <class Cfg>
+cudaError_t grouped_cfg(bool prepare, const TcArgs* args, const int* first, int nprob, int total, bool qm_small,
+                        size_t smem, cudaStream_t s) {
+  if (prepare) {
+    // the limit is per kernel and process-wide: only ever raise it
+    auto kern = qm_small ? mttkrp_tc_grouped_kernel<Cfg, 2> : mttkrp_tc_grouped_kernel<Cfg, kMaxModes - 2>;
+    cudaFuncAttributes fa;
+    const cudaError_t e = cudaFuncGetAttributes(&fa, kern);
+    if (e != cudaSuccess) return e;
+    if ((size_t)fa.maxDynamicSharedSizeBytes >= smem) return cudaSuccess;
+    return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  }
+  if (qm_small)
+    mttkrp_tc_grouped_kernel<Cfg, 2><<<(unsigned)total, kThreads, smem, s>>>(args, first, nprob);
+  else
+    mttkrp_tc_grouped_kernel<Cfg, kMaxModes - 2><<<(unsigned)total, kThreads, smem, s>>>(args, first, nprob);
+  return cudaGetLastError();
+}
+
+cudaError_t grouped_dispatch(int precision, bool prepare, const TcArgs* args, const int* first, int nprob, int total,
+                             bool qm_small, size_t smem, cudaStream_t s) {
+  switch (precision) {
+    case JKCALS_TF32: return grouped_cfg<CfgTF32>(prepare, args, first, nprob, total, qm_small, smem, s);
+    case JKCALS_3XTF32: return grouped_cfg<Cfg3xTF32>(prepare, args, first, nprob, total, qm_small, smem, s);
+    case JKCALS_BF16: return grouped_cfg<CfgBF16>(prepare, args, first, nprob, total, qm_small, smem, s);
+    case JKCALS_SPLIT_BF16: return grouped_cfg<CfgBF16x3>(prepare, args, first, nprob, total, qm_small, smem, s);
+    case JKCALS_EXACT_BF16: return grouped_cfg<CfgExact>(prepare, args, first, nprob, total, qm_small, smem, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 }  // namespace
+
+cudaError_t prepare_mttkrp_tc_grouped(int precision, bool qm_small, size_t smem) {
+  return grouped_dispatch(precision, true, nullptr, nullptr, 0, 0, qm_small, smem, nullptr);
+}
+
+cudaError_t launch_mttkrp_tc_grouped(int precision, const TcArgs* args, const int* first, int nprob, int total,
+                                     bool qm_small, size_t smem, cudaStream_t s) {
+  return grouped_dispatch(precision, false, args, first, nprob, total, qm_small, smem, s);
+}
 
 int form_nsplit(int precision) {
   switch (precision) {

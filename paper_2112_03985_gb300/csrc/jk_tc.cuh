@@ -57,6 +57,7 @@ struct TcArgs {
   const unsigned char* At;         // sliced, pre-tiled U_a^T: per 128-row tile and k-step one A stage image
   int nkt_a, n_o, o_per_cta, nbuf;
   int nis;                         // MMA-issuing threads (1 or 2), each with S / nis ring stages
+  int tiles_c, tiles_n;            // grid of this problem (C tiles x N tiles x splits): grouped launches
   int Ia;                          // size of mode a
   int64_t ut_stride_a;             // row stride of UTa / UTa_lo (floats)
   int skip_slice;                  // At already holds the current slices of U_a
@@ -76,6 +77,13 @@ int build_mma_list(int precision, TcPlan& p);
 // Raise the kernel's dynamic shared-memory limit (call once, outside stream capture).
 cudaError_t prepare_mttkrp_tc(int precision, size_t max_smem);
 cudaError_t launch_mttkrp_tc(int precision, const TcPlan& p, const TcArgs& a, cudaStream_t s);
+// The one-step MTTKRPs of several problems in one launch (the two-step form is
+// not grouped): args[b] (device) is problem b's TcArgs, first[b] its first CTA
+// (nprob + 1 entries, first[nprob] = total); qm_small: every problem has at most
+// two remaining modes (nq <= 2); smem: the largest problem's tc_smem_bytes.
+cudaError_t prepare_mttkrp_tc_grouped(int precision, bool qm_small, size_t smem);
+cudaError_t launch_mttkrp_tc_grouped(int precision, const TcArgs* args, const int* first, int nprob, int total,
+                                     bool qm_small, size_t smem, cudaStream_t s);
 // Bytes of the A images of a two-step plan (tiles_c x nkt_a stage images).
 size_t tts_a_bytes(const TcPlan& p);
 

@@ -284,6 +284,11 @@ __global__ void advance_sweep_kernel(int* sweep_idx) {
   if (threadIdx.x == 0 && blockIdx.x == 0) *sweep_idx += 1;
 }
 
+// the sweep counters of several problems (a grouped batch sweep)
+__global__ void advance_sweeps_kernel(int* const* sweep_idx, int n) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) *sweep_idx[i] += 1;
+}
+
 // ---- gradient ---------------------------------------------------------------
 
 struct GradArgs {
@@ -379,6 +384,11 @@ cudaError_t launch_update(const UpdateArgs& a, cudaStream_t s) {
 
 cudaError_t launch_advance_sweep(int* sweep_idx, cudaStream_t s) {
   advance_sweep_kernel<<<1, 32, 0, s>>>(sweep_idx);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_advance_sweeps(int* const* sweep_idx, int n, cudaStream_t s) {
+  advance_sweeps_kernel<<<(n + 127) / 128, 128, 0, s>>>(sweep_idx, n);
   return cudaGetLastError();
 }
 

@@ -19,6 +19,8 @@
 // there are enough blocks to fill the GPU; otherwise the two-phase update runs.
 #include <math.h>
 
+#include <string>
+
 #include "jk_common.cuh"
 
 namespace jk {
@@ -77,8 +79,7 @@ __device__ __forceinline__ void split_f32_pair(double u, float& hi, float& lo) {
 // RMAX bounds the rank of every block; FIXED means every block has exactly RMAX
 // components, so the per-rank guards fold away at compile time.
 template <int RMAX, bool FIXED>
-__global__ void __launch_bounds__(NT, FIXED ? 4 : 2) update_fused_kernel(UpdateArgs a) {
-  const int g = blockIdx.x;
+__device__ __forceinline__ void update_fused_body(const UpdateArgs& a, int g, double* X) {
   const int tid = threadIdx.x;
   const bool last = (a.n == a.N - 1);
   const int sweep = last ? *a.sweep_idx : 0;
@@ -92,7 +93,7 @@ __global__ void __launch_bounds__(NT, FIXED ? 4 : 2) update_fused_kernel(UpdateA
   const int64_t I = a.I;
   const int64_t count = I * (int64_t)a.C;   // elements of one partial
 
-  extern __shared__ double X[];             // I x R rows of this block
+  // X: I x R rows of this block, dynamic shared memory
   __shared__ double L[RMAX][RMAX + 1];      // H, then its Cholesky factor
   __shared__ double Hc[RMAX * RMAX];        // H kept for the error
   __shared__ double G[RMAX][RMAX + 1];
@@ -390,6 +391,12 @@ __global__ void __launch_bounds__(NT, FIXED ? 4 : 2) update_fused_kernel(UpdateA
   }
 }
 
+template <int RMAX, bool FIXED>
+__global__ void __launch_bounds__(NT, FIXED ? 4 : 2) update_fused_kernel(UpdateArgs a) {
+  extern __shared__ double X[];
+  update_fused_body<RMAX, FIXED>(a, blockIdx.x, X);
+}
+
 // Wide form of the same update for ranks <= 7: one CTA per block, warp 0 forms
 // H and its Cholesky factor while up to 224 row threads (one or two rows each, or more)
 // sum their rows' split-K partials; then every row thread solves its rows and
@@ -407,14 +414,24 @@ __host__ __device__ constexpr int wide_npad(int rmax) {
   return rmax * (rmax + 1) / 2 + 1 <= 16 ? 16 : 32;
 }
 
+// Row threads of the wide update of a mode with I rows: one row each for I <= 128
+// (those updates are bound by one block's chain of dependent operations), two
+// for wider ones (fewer warps, so fewer FP64 adds in the cross-lane reduction).
+__host__ __device__ inline int wide_row_threads(int64_t I) {
+  int64_t rt = I <= 128 ? (I + 31) / 32 * 32 : ((I + 1) / 2 + 31) / 32 * 32;
+  return (int)(rt > kWideRows ? kWideRows : rt);
+}
+
+// Block g of one problem; the CTA has at least 32 + wide_row_threads(a.I)
+// threads; the ones beyond take no rows but meet every barrier.
 template <int RMAX, bool FIXED>
-__global__ void __launch_bounds__(kWideRows + 32, 1) update_wide_kernel(UpdateArgs a) {
+__device__ __forceinline__ void update_wide_body(const UpdateArgs& a, int g, double* X) {
   constexpr int NP = RMAX * (RMAX + 1) / 2;   // Gram entries (upper triangle), then the fit term
   constexpr int NPAD = wide_npad(RMAX);
-  const int g = blockIdx.x;
   const int tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5;
-  const int RT = (int)blockDim.x - 32;        // row threads
+  const int RT = wide_row_threads(a.I);       // row threads
+  const bool rows = warp > 0 && tid < 32 + RT;   // this thread takes rows
   const bool last = (a.n == a.N - 1);
   const int sweep = last ? *a.sweep_idx : 0;
   const double qnan = __longlong_as_double(0x7ff8000000000000LL);
@@ -427,7 +444,7 @@ __global__ void __launch_bounds__(kWideRows + 32, 1) update_wide_kernel(UpdateAr
   const int64_t I = a.I;
   const int64_t count = I * (int64_t)a.C;   // elements of one partial
 
-  extern __shared__ double X[];             // I x R rows of this block (Mbar rows, then the solutions)
+  // X: I x R rows of this block (Mbar rows, then the solutions), dynamic shared memory
   __shared__ double L[RMAX][RMAX + 1];
   __shared__ double Hc[RMAX * RMAX];
   __shared__ double invd[RMAX];
@@ -474,7 +491,7 @@ __global__ void __launch_bounds__(kWideRows + 32, 1) update_wide_kernel(UpdateAr
     // order; the partials are loaded PB splits at a time (all in flight together)
     // and then added in order, one memory round trip per batch
     constexpr int PB = RMAX <= 4 ? 8 : 4;
-    for (int64_t i = tid - 32; i < I; i += RT) {
+    for (int64_t i = tid - 32; rows && i < I; i += RT) {
       double v[RMAX];
       if (a.part_kind == kPartF64) {
         const double* P = reinterpret_cast<const double*>(a.part);
@@ -545,7 +562,7 @@ __global__ void __launch_bounds__(kWideRows + 32, 1) update_wide_kernel(UpdateAr
   double acc[NPAD];
 #pragma unroll
   for (int p = 0; p < NPAD; ++p) acc[p] = 0.0;
-  if (warp > 0) {
+  if (rows) {
     for (int64_t i = tid - 32; i < I; i += RT) {
       double x[RMAX], m[RMAX];
 #pragma unroll
@@ -625,7 +642,7 @@ __global__ void __launch_bounds__(kWideRows + 32, 1) update_wide_kernel(UpdateAr
     }
   }
   __syncthreads();
-  const int nw = (int)blockDim.x >> 5;
+  const int nw = (int)blockDim.x >> 5;   // warps beyond 32 + RT threads hold zeros
   if (tid <= NP) {
     double sacc = wsum[0][tid];
     for (int w = 1; w < nw; ++w) sacc += wsum[w][tid];
@@ -653,7 +670,7 @@ __global__ void __launch_bounds__(kWideRows + 32, 1) update_wide_kernel(UpdateAr
   float cm[RMAX];
 #pragma unroll
   for (int r = 0; r < RMAX; ++r) cm[r] = 0.f;
-  if (warp > 0) {
+  if (rows) {
     for (int64_t i = tid - 32; i < I; i += RT) {
 #pragma unroll
       for (int r = 0; r < RMAX; ++r) {
@@ -706,6 +723,52 @@ __global__ void __launch_bounds__(kWideRows + 32, 1) update_wide_kernel(UpdateAr
   a.loss_prev[g] = e;
 }
 
+template <int RMAX, bool FIXED>
+__global__ void __launch_bounds__(kWideRows + 32, 1) update_wide_kernel(UpdateArgs a) {
+  extern __shared__ double X[];
+  update_wide_body<RMAX, FIXED>(a, blockIdx.x, X);
+}
+
+// Block x of a grouped launch belongs to problem b with first[b] <= x < first[b + 1].
+__device__ __forceinline__ int group_problem_u(const int* first, int nprob, int x) {
+  int lo = 0, hi = nprob - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (__ldg(first + mid) <= x) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ void load_args(UpdateArgs& sa, const UpdateArgs* args, int b) {
+  const uint32_t* src = reinterpret_cast<const uint32_t*>(args + b);
+  uint32_t* dst = reinterpret_cast<uint32_t*>(&sa);
+  for (int i = threadIdx.x; i < (int)(sizeof(UpdateArgs) / 4); i += blockDim.x) dst[i] = __ldg(src + i);
+}
+
+template <int RMAX, bool FIXED>
+__global__ void __launch_bounds__(kWideRows + 32, 1) update_wide_grouped_kernel(const UpdateArgs* __restrict__ args,
+                                                                               const int* __restrict__ first,
+                                                                               int nprob) {
+  extern __shared__ double X[];
+  __shared__ __align__(16) UpdateArgs sa;
+  const int b = group_problem_u(first, nprob, (int)blockIdx.x);
+  load_args(sa, args, b);
+  __syncthreads();
+  update_wide_body<RMAX, FIXED>(sa, (int)blockIdx.x - __ldg(first + b), X);
+}
+
+template <int RMAX, bool FIXED>
+__global__ void __launch_bounds__(NT, 2) update_fused_grouped_kernel(const UpdateArgs* __restrict__ args,
+                                                                                const int* __restrict__ first,
+                                                                                int nprob) {
+  extern __shared__ double X[];
+  __shared__ __align__(16) UpdateArgs sa;
+  const int b = group_problem_u(first, nprob, (int)blockIdx.x);
+  load_args(sa, args, b);
+  __syncthreads();
+  update_fused_body<RMAX, FIXED>(sa, (int)blockIdx.x - __ldg(first + b), X);
+}
+
 template <int RM, bool F>
 cudaError_t run_wide(const UpdateArgs* a, size_t smem, cudaStream_t s, bool prepare) {
   if (prepare) {
@@ -715,12 +778,7 @@ cudaError_t run_wide(const UpdateArgs* a, size_t smem, cudaStream_t s, bool prep
     if ((size_t)fa.maxDynamicSharedSizeBytes >= smem) return cudaSuccess;
     return cudaFuncSetAttribute(update_wide_kernel<RM, F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   }
-  // one row per thread for narrow modes (their updates are bound by one block's
-  // chain of dependent operations), two for wider ones (fewer warps, so fewer
-  // FP64 adds in the cross-lane reduction of the Gram)
-  int64_t rt = a->I <= 128 ? (a->I + 31) / 32 * 32 : ((a->I + 1) / 2 + 31) / 32 * 32;
-  if (rt > kWideRows) rt = kWideRows;
-  update_wide_kernel<RM, F><<<a->K, (unsigned)(rt + 32), smem, s>>>(*a);
+  update_wide_kernel<RM, F><<<a->K, (unsigned)(wide_row_threads(a->I) + 32), smem, s>>>(*a);
   return cudaGetLastError();
 }
 
@@ -761,7 +819,69 @@ static cudaError_t dispatch_fused(const UpdateArgs* a, size_t smem, int Rmax, bo
   return run_fused<32, false>(a, smem, s, prepare);
 }
 
+std::string g_grouped_attrs;   // attributes of the last grouped update kernel launched (diagnostics)
+
+template <class KF>
+cudaError_t run_grouped(KF kernel, bool prepare, unsigned threads, const UpdateArgs* args, const int* first,
+                        int nprob, int total, size_t smem, cudaStream_t s) {
+  if (prepare) {
+    // the limit is per kernel and process-wide: only ever raise it
+    cudaFuncAttributes fa{};
+    const cudaError_t e = cudaFuncGetAttributes(&fa, kernel);
+    if (e != cudaSuccess) return e;
+    if ((size_t)fa.maxDynamicSharedSizeBytes >= smem) return cudaSuccess;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  }
+  cudaFuncAttributes fa{};
+  if (cudaFuncGetAttributes(&fa, kernel) == cudaSuccess)
+    g_grouped_attrs = "max threads " + std::to_string(fa.maxThreadsPerBlock) + ", registers " +
+                      std::to_string(fa.numRegs) + ", static smem " + std::to_string(fa.sharedSizeBytes) +
+                      ", max dynamic smem " + std::to_string(fa.maxDynamicSharedSizeBytes);
+  kernel<<<(unsigned)total, threads, smem, s>>>(args, first, nprob);
+  return cudaGetLastError();
+}
+
+// The same instance that dispatch_fused picks for (Rmax, uniform), grouped;
+// threads: the largest CTA that a problem of the group takes on its own.
+cudaError_t dispatch_grouped(bool prepare, const UpdateArgs* args, const int* first, int nprob, int total,
+                             int threads, int Rmax, bool uniform, size_t smem, cudaStream_t s) {
+  const unsigned tw = (unsigned)threads;
+  if (uniform) {
+    switch (Rmax) {
+      case 1: return run_grouped(update_wide_grouped_kernel<1, true>, prepare, tw, args, first, nprob, total, smem, s);
+      case 2: return run_grouped(update_wide_grouped_kernel<2, true>, prepare, tw, args, first, nprob, total, smem, s);
+      case 3: return run_grouped(update_wide_grouped_kernel<3, true>, prepare, tw, args, first, nprob, total, smem, s);
+      case 4: return run_grouped(update_wide_grouped_kernel<4, true>, prepare, tw, args, first, nprob, total, smem, s);
+      case 5: return run_grouped(update_wide_grouped_kernel<5, true>, prepare, tw, args, first, nprob, total, smem, s);
+      case 6: return run_grouped(update_wide_grouped_kernel<6, true>, prepare, tw, args, first, nprob, total, smem, s);
+      case 7: return run_grouped(update_wide_grouped_kernel<7, true>, prepare, tw, args, first, nprob, total, smem, s);
+      case 8:
+        return run_grouped(update_fused_grouped_kernel<8, true>, prepare, NT, args, first, nprob, total, smem, s);
+      default: break;
+    }
+  }
+  if (Rmax <= 8) return run_grouped(update_fused_grouped_kernel<8, false>, prepare, NT, args, first, nprob, total, smem, s);
+  if (Rmax <= 16)
+    return run_grouped(update_fused_grouped_kernel<16, false>, prepare, NT, args, first, nprob, total, smem, s);
+  return run_grouped(update_fused_grouped_kernel<32, false>, prepare, NT, args, first, nprob, total, smem, s);
+}
+
 }  // namespace
+
+std::string grouped_update_attrs() { return g_grouped_attrs; }
+
+int update_fused_threads(int64_t I, int Rmax, bool uniform) {
+  return (uniform && Rmax <= 7) ? wide_row_threads(I) + 32 : NT;
+}
+
+cudaError_t prepare_update_grouped(int threads, int Rmax, bool uniform, size_t smem) {
+  return dispatch_grouped(true, nullptr, nullptr, 0, 0, threads, Rmax, uniform, smem, nullptr);
+}
+
+cudaError_t launch_update_grouped(const UpdateArgs* args, const int* first, int nprob, int total, int threads,
+                                  int Rmax, bool uniform, size_t smem, cudaStream_t s) {
+  return dispatch_grouped(false, args, first, nprob, total, threads, Rmax, uniform, smem, s);
+}
 
 size_t update_fused_smem(int64_t I, int Rmax) { return (size_t)I * Rmax * sizeof(double); }
 

@@ -1,6 +1,7 @@
 """Register budget of every kernel (no GPU): each translation unit is compiled for sm_103a with
 ptxas' resource report, and no kernel may spill registers to local memory.  One known
-exception is held to its present size: the fused update's generic instantiation for ranks 9-16."""
+exception is held to its present size: the fused update's generic instantiation for ranks 9-16, in its
+per-problem and its grouped (batch) launch."""
 import os
 import re
 import shutil
@@ -15,7 +16,7 @@ CSRC = os.path.join(ROOT, "paper_2112_03985_gb300", "csrc")
 NVCC = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
 
 # mangled-name fragment -> largest allowed spill stores (bytes)
-KNOWN_SPILLS = {"update_fused_kernelILi16ELb0E": 108}
+KNOWN_SPILLS = {"update_fused_kernelILi16ELb0E": 108, "update_fused_grouped_kernelILi16ELb0E": 144}
 
 
 def _report(src, outdir):
