@@ -105,7 +105,11 @@ typedef struct {
                            side and sweep only them (the MTTKRP then spans only their
                            columns); the full layout is restored before jkcals_run returns.
                            0: converged blocks keep their columns until the end           */
-  int reserved[4];
+  int batch_branches;   /* 0 (default): a batch (jkcals_batch_create) whose handles share one
+                           tensor-core form and order runs each kernel step of all problems
+                           as one grouped launch; 1 on any handle of a batch: the batch runs
+                           every problem's own sweep graph as a parallel branch instead     */
+  int reserved[3];
 } jkcals_options;
 
 /* Fill *opt with the defaults above. */
@@ -297,10 +301,20 @@ jkcals_status jkcals_grad(jkcals_t h, const double* const* U, double* const* G, 
  * Batched problems (many independent jackknife problems, each its own handle;
  * configuration 4 of the evaluation).  The paper fits one tensor at a time;
  * batching is a deployment form of Alg. 3 for many small problems, none of
- * which fills the GPU alone.  jkcals_batch_create captures one sweep of every
- * handle and makes them parallel branches (child graphs) of one CUDA graph, so
- * a sweep of the whole batch is one graph launch and the GPU runs the
- * problems' kernels side by side.
+ * which fills the GPU alone.  A sweep of the whole batch is one CUDA graph
+ * launch.  When every handle uses the same tensor-core form, the same tensor
+ * order and the one-step MTTKRP in every mode (and none sets
+ * opt.batch_branches), the graph holds grouped launches: per mode, one MTTKRP
+ * launch over the tiles of all problems (a CTA finds its problem and tile in a
+ * prefix table of tile counts), one fused-update launch per class of
+ * (largest rank, uniform ranks), the remaining problems' reduction and
+ * two-phase update, then one launch that advances every sweep counter.  If any
+ * handle set opt.autotune, the split-K factor of every problem is scaled by 1,
+ * 1/2, 1/4 or 1/8 per mode, each grouped MTTKRP timed, and the fastest kept.
+ * Otherwise each handle's own sweep is captured and the captures become
+ * parallel branches (child graphs) of the batch's graph.  Both forms compute
+ * each problem's sweep exactly as jkcals_als_sweep does (same plans, same
+ * summation order).
  *  handles     n handles, owned by the caller, alive for the batch's lifetime;
  *              no handle may have opt.kernel_timing = 1
  *  max_sweeps  the most sweeps one jkcals_batch_sweep call may run (each

@@ -19,7 +19,7 @@ class Options(ct.Structure):
     _fields_ = [("precision", ct.c_int), ("normalise", ct.c_int), ("use_graph", ct.c_int),
                 ("splits", ct.c_int), ("max_device_bytes", ct.c_int64),
                 ("kernel_timing", ct.c_int), ("update_mode", ct.c_int), ("autotune", ct.c_int),
-                ("compact", ct.c_int), ("reserved", ct.c_int * 4)]
+                ("compact", ct.c_int), ("batch_branches", ct.c_int), ("reserved", ct.c_int * 3)]
 
 
 P = ct.c_void_p

@@ -72,7 +72,7 @@ class JKCALS:
                  init: Sequence, *, precision: str = "fp64", normalise: bool = True,
                  use_graph: bool = True, splits: int = 0, max_device_bytes: int = 0,
                  kernel_timing: bool = False, update_mode: int = 0, autotune: bool = False, compact: bool = True,
-                 stream=None):
+                 batch_branches: bool = False, stream=None):
         lib = L.load()
         self._lib = lib
         self._h = ct.c_void_p()
@@ -94,6 +94,7 @@ class JKCALS:
         opt.update_mode = int(update_mode)
         opt.autotune = int(bool(autotune))
         opt.compact = int(bool(compact))
+        opt.batch_branches = int(bool(batch_branches))
         dims = (ct.c_int64 * self.N)(*self.dims)
         rk = (ct.c_int32 * self.K)(*self.ranks)
         ptr, idx = left_out_csr(left_out)
@@ -283,8 +284,9 @@ class JKCALS:
 
 class Batch:
     """Many independent problems advanced together: one CUDA graph per sweep of
-    the whole batch (jkcals_batch_create / _sweep / _sync / _destroy).  The
-    handles stay owned by the caller and must outlive the batch."""
+    the whole batch, of grouped launches over all problems or of one branch per
+    problem (jkcals_batch_create / _sweep / _sync / _destroy).  The handles stay
+    owned by the caller and must outlive the batch."""
 
     def __init__(self, handles: Sequence[JKCALS], max_sweeps: int, stream=None):
         self._lib = L.load()

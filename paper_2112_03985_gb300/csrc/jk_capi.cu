@@ -130,7 +130,12 @@ void make_plan(jkcals_ctx* h) {
     const int64_t tiles = ((I + kMttkrpBM - 1) / kMttkrpBM) * ((h->C + kMttkrpBN - 1) / kMttkrpBN);
     const int64_t ksteps = (J + kMttkrpBK - 1) / kMttkrpBK;
     int64_t S = h->opt.splits > 0 ? h->opt.splits : (target + tiles - 1) / tiles;
-    if (h->opt.splits <= 0) S = std::min<int64_t>(S, std::max<int64_t>(1, ksteps / 4));
+    // at least 4 k-steps per split, unless the output is small enough that its
+    // partials cost little (at most 64 Ki elements per split): a short
+    // contraction then still spreads over the SMs (GB300 runs about two FP64
+    // FMAs per clock and SM, so a few busy SMs bound a small mode)
+    const int64_t min_ksteps = I * h->C <= 65536 ? 1 : 4;
+    if (h->opt.splits <= 0) S = std::min<int64_t>(S, std::max<int64_t>(1, ksteps / min_ksteps));
     S = std::max<int64_t>(1, std::min<int64_t>(S, ksteps));
     int64_t kchunk = ((ksteps + S - 1) / S) * kMttkrpBK;
     S = (J + kchunk - 1) / kchunk;
@@ -1561,10 +1566,12 @@ struct jkcals_batch_ctx {
 namespace {
 
 // A batch sweep runs as grouped launches when every problem uses the same
-// tensor-core form and order and no mode takes the two-step form.
+// tensor-core form and order, no mode takes the two-step form and no handle
+// asked for per-problem branches.
 bool batch_groupable(const std::vector<jkcals_ctx*>& hs) {
   for (jkcals_ctx* h : hs) {
-    if (!h->tc || h->opt.precision != hs[0]->opt.precision || h->N != hs[0]->N) return false;
+    if (h->opt.batch_branches || !h->tc || h->opt.precision != hs[0]->opt.precision || h->N != hs[0]->N)
+      return false;
     for (int n = 0; n < h->N; ++n)
       if (h->tcplan[n].tts) return false;
   }
@@ -1665,9 +1672,10 @@ jkcals_status autotune_grouped(jkcals_batch_ctx* b) {
 }
 
 // Captures one grouped sweep of every problem on the batch's stream: per mode,
-// one MTTKRP launch for all problems, one fused-update launch per rank class
-// (each problem's block arithmetic is that of its own sweep), the other
-// problems' split-K reduction and two-phase update, then every sweep counter.
+// one MTTKRP launch for all problems, then side by side one fused-update launch
+// per rank class (each problem's block arithmetic is that of its own sweep) and
+// the other problems' split-K reduction and two-phase update; after the last
+// mode, every sweep counter.
 jkcals_status capture_grouped(jkcals_batch_ctx* b, cudaGraph_t* graph) {
   const int P = (int)b->hs.size();
   const int N = b->hs[0]->N;
@@ -1715,15 +1723,50 @@ jkcals_status capture_grouped(jkcals_batch_ctx* b, cudaGraph_t* graph) {
   void* dc = nullptr;
   JK_TRY(batch_upload(b, &dc, counters.data(), sizeof(int*) * P));
 
-  cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
-  if (e != cudaSuccess) return fail(JKCALS_ERR_CUDA, std::string("cudaStreamBeginCapture: ") + cudaGetErrorString(e));
+  // The update launches of one mode touch disjoint problems: each runs on a
+  // side stream forked from the batch's stream after the grouped MTTKRP and
+  // joined before the next mode, so the graph holds them as parallel nodes.
+  size_t nside = 1;
+  for (int n = 0; n < N; ++n) nside = std::max(nside, upd[n].size() + 1);
+  std::vector<cudaStream_t> side(nside, nullptr);
+  std::vector<cudaEvent_t> evs;
+  auto cleanup = [&]() {
+    for (cudaStream_t x : side)
+      if (x) cudaStreamDestroy(x);
+    for (cudaEvent_t x : evs) cudaEventDestroy(x);
+  };
+  cudaError_t e = cudaSuccess;
+  for (cudaStream_t& x : side)
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking);
+  // one fork event per mode and one join event per (mode, side stream)
+  for (size_t k = 0; e == cudaSuccess && k < (size_t)N * (nside + 1); ++k) {
+    cudaEvent_t x = nullptr;
+    e = cudaEventCreateWithFlags(&x, cudaEventDisableTiming);
+    if (e == cudaSuccess) evs.push_back(x);
+  }
+  if (e != cudaSuccess) {
+    cleanup();
+    return fail(JKCALS_ERR_CUDA, std::string("batch side streams: ") + cudaGetErrorString(e));
+  }
+  e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) {
+    cleanup();
+    return fail(JKCALS_ERR_CUDA, std::string("cudaStreamBeginCapture: ") + cudaGetErrorString(e));
+  }
   jkcals_status st = JKCALS_OK;
   for (int n = 0; n < N && st == JKCALS_OK; ++n) {
     st = launch_grouped_mttkrp(b, mt[n]);
-    for (const UpdClass& c : upd[n]) {
+    cudaEvent_t fork = evs[(size_t)n * (nside + 1)];
+    if (st == JKCALS_OK && (e = cudaEventRecord(fork, b->stream)) != cudaSuccess)
+      st = fail(JKCALS_ERR_CUDA, std::string("batch fork: ") + cudaGetErrorString(e));
+    for (size_t k = 0; k < nside && st == JKCALS_OK; ++k)
+      if ((e = cudaStreamWaitEvent(side[k], fork, 0)) != cudaSuccess)
+        st = fail(JKCALS_ERR_CUDA, std::string("batch fork: ") + cudaGetErrorString(e));
+    for (size_t ci = 0; ci < upd[n].size(); ++ci) {
+      const UpdClass& c = upd[n][ci];
       if (st != JKCALS_OK) break;
       e = launch_update_grouped(c.dargs, c.dfirst, (int)c.args.size(), c.first.back(), c.threads, c.Rmax, c.uniform,
-                                c.smem, b->stream);
+                                c.smem, side[ci]);
       if (e != cudaSuccess)
         st = fail(JKCALS_ERR_CUDA, std::string("grouped update (mode ") + std::to_string(n) + ", rank class " +
                                        std::to_string(c.Rmax) + (c.uniform ? " uniform" : " mixed") + ", " +
@@ -1731,14 +1774,20 @@ jkcals_status capture_grouped(jkcals_batch_ctx* b, cudaGraph_t* graph) {
                                        " B dynamic shared memory, " + std::to_string(c.first.back()) +
                                        " blocks; " + grouped_update_attrs() + "): " + cudaGetErrorString(e));
     }
+    cudaStream_t s2 = side[nside - 1];   // the other problems' reduction and two-phase update
     for (jkcals_ctx* h : b->hs) {
       if (st != JKCALS_OK || h->plan[n].upd.fused) continue;
       const int64_t cnt = h->dims[n] * (int64_t)h->C;
       e = part_kind(h) == kPartF32x2
-              ? launch_reduce_partials_f32x2(static_cast<float2*>(h->part), mode_splits(h, n), cnt, h->mbuf, b->stream)
-              : launch_reduce_partials_f32(static_cast<float*>(h->part), mode_splits(h, n), cnt, h->mbuf, b->stream);
-      if (e == cudaSuccess) e = launch_update(update_args(h, n, h->mbuf, kPartF64, 1), b->stream);
+              ? launch_reduce_partials_f32x2(static_cast<float2*>(h->part), mode_splits(h, n), cnt, h->mbuf, s2)
+              : launch_reduce_partials_f32(static_cast<float*>(h->part), mode_splits(h, n), cnt, h->mbuf, s2);
+      if (e == cudaSuccess) e = launch_update(update_args(h, n, h->mbuf, kPartF64, 1), s2);
       if (e != cudaSuccess) st = fail(JKCALS_ERR_CUDA, std::string("batched two-phase update: ") + cudaGetErrorString(e));
+    }
+    for (size_t k = 0; k < nside && st == JKCALS_OK; ++k) {
+      cudaEvent_t join = evs[(size_t)n * (nside + 1) + 1 + k];
+      if ((e = cudaEventRecord(join, side[k])) != cudaSuccess || (e = cudaStreamWaitEvent(b->stream, join, 0)) != cudaSuccess)
+        st = fail(JKCALS_ERR_CUDA, std::string("batch join: ") + cudaGetErrorString(e));
     }
   }
   if (st == JKCALS_OK) {
@@ -1746,6 +1795,7 @@ jkcals_status capture_grouped(jkcals_batch_ctx* b, cudaGraph_t* graph) {
     if (e != cudaSuccess) st = fail(JKCALS_ERR_CUDA, std::string("sweep counters: ") + cudaGetErrorString(e));
   }
   e = cudaStreamEndCapture(b->stream, graph);
+  cleanup();
   if (st != JKCALS_OK) {
     if (*graph) cudaGraphDestroy(*graph);
     *graph = nullptr;

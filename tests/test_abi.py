@@ -52,11 +52,25 @@ def test_binding_loads_without_gpu(built_lib):
     opt = _lib.Options()
     lib.jkcals_default_options(ctypes.byref(opt))
     assert opt.precision == 0 and opt.normalise == 1 and opt.use_graph == 1
+    assert opt.compact == 1 and opt.batch_branches == 0 and opt.autotune == 0
+
+
+def header_option_fields():
+    text = open(os.path.join(ROOT, "include", "jkcals.h")).read()
+    body = re.search(r"typedef struct \{(.*?)\} jkcals_options;", text, flags=re.S).group(1)
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    return [(m.group(1), m.group(2), int(m.group(3) or 1))
+            for m in re.finditer(r"\b(int|int64_t)\s+(\w+)(?:\[(\d+)\])?\s*;", body)]
 
 
 def test_options_struct_layout_matches_header():
     from paper_2112_03985_gb300 import _lib
-    # int,int,int,int,int64,int[8] -> 4*4 + 8 + 32 = 56 bytes
+    fields = header_option_fields()
+    assert [f[1] for f in fields] == [f[0] for f in _lib.Options._fields_]
+    for (ctype, name, count), (pname, ptype) in zip(fields, _lib.Options._fields_):
+        base = ctypes.c_int64 if ctype == "int64_t" else ctypes.c_int
+        assert ctypes.sizeof(ptype) == ctypes.sizeof(base) * count, name
+    # int x 4, int64, int x 8 (with the reserved words) -> 16 + 8 + 32 = 56 bytes, as before
     assert ctypes.sizeof(_lib.Options) == 56
 
 

@@ -1,7 +1,9 @@
 """Configuration 4: a batch of independent LOO jackknife problems of uneven
 sizes and ranks (I1 in [20, 400], I2, I3 in [30, 150], R in [2, 8], FP32),
-advanced together by one CUDA graph per sweep (jkcals_batch_*), with the split
-factors picked by the autotuner (opt.autotune)."""
+advanced together by one CUDA graph per sweep (jkcals_batch_*): grouped
+launches over all problems when they share a one-step tensor-core form, else
+(or with opt.batch_branches) one graph branch per problem; the split factors
+picked by the autotuner (opt.autotune)."""
 import numpy as np
 import pytest
 
@@ -29,11 +31,15 @@ def _handles(ws, **kw):
     return [api.from_workload(w, device="cuda", **kw) for w in ws]
 
 
-def test_batched_sweeps_equal_individual_sweeps(problems):
+@pytest.mark.parametrize("precision,branches", [("3xtf32", False), ("3xtf32", True), ("exact_bf16", False)])
+def test_batched_sweeps_equal_individual_sweeps(problems, precision, branches):
+    """Both batch forms (grouped launches; per-problem branches, which the
+    exact-chain form's two-step modes also take) compute each problem's sweep
+    bit for bit as its own handle does."""
     _cuda()
     ws = problems[:8]
-    hs_a = _handles(ws, precision="3xtf32")
-    hs_b = _handles(ws, precision="3xtf32")
+    hs_a = _handles(ws, precision=precision)
+    hs_b = _handles(ws, precision=precision, batch_branches=branches)
     try:
         ref = [(h.als_sweep(5), h.get_factors()) for h in hs_a]
         with api.Batch(hs_b, max_sweeps=5) as b:

@@ -52,6 +52,18 @@ def test_plan_invariants(prec, dims):
             assert m["splits"] <= others // big        # whole index values o per split
 
 
+def test_fp64_small_modes_spread_over_the_sms():
+    """20x30x40, 21 rank-3 blocks: each mode's output is 64 x 64 at most, so the FP64
+    MTTKRP splits down to one k-step of 16 columns of J per CTA rather than four,
+    filling about half of 148 SMs instead of a tenth; larger outputs keep four."""
+    p = api.plan_query((20, 30, 40), [3] * 21, "fp64", num_sms=148)
+    J = [30 * 40, 20 * 40, 20 * 30]
+    assert [m["splits"] for m in p] == [-(-j // 16) for j in J]
+    big = api.plan_query((300, 100, 50), [5] * 300, "fp64", num_sms=148)
+    ksteps = [-(-j // 16) for j in (5000, 15000, 30000)]
+    assert all(m["splits"] <= k // 4 for m, k in zip(big, ksteps))
+
+
 def test_user_split_factor_is_kept():
     p = api.plan_query((20, 30, 40), [3] * 21, "fp64", splits=3)
     assert [m["splits"] for m in p] == [3, 3, 3]
