@@ -1026,7 +1026,10 @@ __global__ void slice_a_kernel(const float* __restrict__ UT, const float* __rest
   }
 }
 
-template <int QM>
+// VAR: the B parts stacked per MMA (4, 2 or 1; from the plan's stack), fixed at
+// compile time: a runtime switch over the variants costs the issuing lane about
+// 50 cycles per stage, where a stage has ~700 cycles of tensor work.
+template <int QM, int VAR>
 __global__ void __launch_bounds__(kThreads, 1) mttkrp_tts_kernel(const TcArgs a) {
   using Cfg = CfgExact;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -1132,7 +1135,6 @@ __global__ void __launch_bounds__(kThreads, 1) mttkrp_tts_kernel(const TcArgs a)
       for (int c = 0; c < 5; ++c)
         idesc[c] = (1u << 4) | ((uint32_t)Cfg::fmt << 7) | ((uint32_t)Cfg::fmt << 10) |
                    (((uint32_t)(c * a.BN) >> 3) << 17) | ((uint32_t)(kRowsM >> 4) << 24);
-      const int variant = a.stack >= 4 ? 4 : a.stack;
       bool ok = true;
       int jj = 0, kin = 0;   // this issuer's o and the k-step within it
       int j = e, b = e % nbuf;   // o of the CTA and its accumulator set
@@ -1152,15 +1154,7 @@ __global__ void __launch_bounds__(kThreads, 1) mttkrp_tts_kernel(const TcArgs a)
         tc_fence_after();
         const uint64_t ad0 = desc0 + (uint64_t)(((uint32_t)st * stage_bytes) >> 4);
         const uint64_t bd0 = ad0 + (uint64_t)(a_stage >> 4);
-        {
-          constexpr int KS = ROW / 32;
-          const bool first = kin == 0;
-          switch (variant) {
-            case 4: issue_stage<Cfg, 4, false, KS>(td, ad0, bd0, L, b16, idesc, first); break;
-            case 2: issue_stage<Cfg, 2, false, KS>(td, ad0, bd0, L, b16, idesc, first); break;
-            default: issue_stage<Cfg, 1, false, KS>(td, ad0, bd0, L, b16, idesc, first); break;
-          }
-        }
+        issue_stage<Cfg, VAR, false, ROW / 32>(td, ad0, bd0, L, b16, idesc, kin == 0);
         tc_commit(&empty[st]);
         if (++kin == nkt_a) {
           tc_commit(&accum[b]);   // o j complete in set b
@@ -1330,13 +1324,33 @@ cudaError_t set_smem_cfg(size_t smem) {
   return set_smem_cfg1<Cfg, kMaxModes - 2>(smem);
 }
 
-template <int QM>
-cudaError_t set_smem_tts1(size_t smem) {
+template <int QM, int VAR>
+cudaError_t set_smem_tts2(size_t smem) {
   cudaFuncAttributes fa;
-  const cudaError_t e = cudaFuncGetAttributes(&fa, mttkrp_tts_kernel<QM>);
+  const cudaError_t e = cudaFuncGetAttributes(&fa, mttkrp_tts_kernel<QM, VAR>);
   if (e != cudaSuccess) return e;
   if ((size_t)fa.maxDynamicSharedSizeBytes >= smem) return cudaSuccess;
-  return cudaFuncSetAttribute(mttkrp_tts_kernel<QM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  return cudaFuncSetAttribute(mttkrp_tts_kernel<QM, VAR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+template <int QM>
+cudaError_t set_smem_tts1(size_t smem) {
+  cudaError_t e = set_smem_tts2<QM, 4>(smem);
+  if (e == cudaSuccess) e = set_smem_tts2<QM, 2>(smem);
+  if (e == cudaSuccess) e = set_smem_tts2<QM, 1>(smem);
+  return e;
+}
+
+// stacking variant of the two-step kernel for a plan's stack (issue_stage's G)
+inline int tts_variant(int stack) { return stack >= 4 ? 4 : (stack == 2 ? 2 : 1); }
+
+template <int QM>
+void launch_tts_qm(dim3 grid, size_t smem, cudaStream_t s, const TcArgs& a) {
+  switch (tts_variant(a.stack)) {
+    case 4: mttkrp_tts_kernel<QM, 4><<<grid, kThreads, smem, s>>>(a); break;
+    case 2: mttkrp_tts_kernel<QM, 2><<<grid, kThreads, smem, s>>>(a); break;
+    default: mttkrp_tts_kernel<QM, 1><<<grid, kThreads, smem, s>>>(a); break;
+  }
 }
 
 cudaError_t launch_tts(const TcPlan& p, const TcArgs& a, cudaStream_t s) {
@@ -1354,9 +1368,9 @@ cudaError_t launch_tts(const TcPlan& p, const TcArgs& a, cudaStream_t s) {
   const size_t smem = tc_smem_bytes(p);
   dim3 grid((unsigned)p.tiles_c, (unsigned)p.tiles_n, (unsigned)p.splits);
   if (a.nq <= 2)
-    mttkrp_tts_kernel<2><<<grid, kThreads, smem, s>>>(a);
+    launch_tts_qm<2>(grid, smem, s, a);
   else
-    mttkrp_tts_kernel<kMaxModes - 2><<<grid, kThreads, smem, s>>>(a);
+    launch_tts_qm<kMaxModes - 2>(grid, smem, s, a);
   return cudaGetLastError();
 }
 
