@@ -1093,8 +1093,40 @@ __global__ void __launch_bounds__(kThreads, 1) mttkrp_tts_kernel(const TcArgs a)
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
 
-  if (warp == 0) {
-    // ---------------- TMA: lane s loads ring stage s (A image and B image) --------
+  if (warp == 0 && nis == 1) {
+    // ---------------- TMA: one lane refills the ring in order --------------------
+    // k-step it of the CTA (o = it / nkt_a, k-step kk within it) goes to stage
+    // it mod S.  One lane in order, rather than lane s for stage s: diverged
+    // lanes of one warp blocked in their own barrier waits delay each other's
+    // refills.
+    if (lane == 0) {
+      const int nke = nseg * nkt_a;
+      int issued = 0;
+      const unsigned char* srcb = a.Tt + ((int64_t)blockIdx.y * a.nkt + (int64_t)o0 * nkt_a) * (int64_t)b_stage;
+      const unsigned char* srca = a.At + (int64_t)blockIdx.x * nkt_a * (int64_t)a_stage;
+      int s = 0, kk = 0;
+      uint32_t ph = 0;
+      for (int it = 0; it < nke; ++it) {
+        if (!wait_bounded(&empty[s], ph ^ 1u, abort_flag, a.err, 1)) break;
+        unsigned char* dst = ring + (size_t)s * stage_bytes;
+        mbar_arrive_expect_tx(&full[s], a_stage + b_stage);
+        bulk_load(dst, srca + (int64_t)kk * a_stage, a_stage, &full[s]);
+        bulk_load(dst + a_stage, srcb + (int64_t)it * b_stage, b_stage, &full[s]);
+        issued = it + 1;
+        if (++kk == nkt_a) kk = 0;
+        if (++s == S) {
+          s = 0;
+          ph ^= 1u;
+        }
+      }
+      if (*abort_flag && issued > 0) {
+        const uint64_t t0 = global_ns();
+        while (global_ns() - t0 < 200000ull) {
+        }
+      }
+    }
+  } else if (warp == 0) {
+    // ---------------- TMA (two issuers): lane s loads ring stage s -----------------
     // Stage s belongs to issuer e = s / Sh; it carries that issuer's k-steps
     // it = s - e Sh, + Sh, ... (k-step kk of its o number it / nkt_a).
     if (lane < S) {
