@@ -1,5 +1,6 @@
 // Fused per-submodel update, one CTA per block (Alg. 3, the loop over p inside
-// the mode loop), all arithmetic in FP64.  Input: the S split-K partials of the
+// the mode loop), in FP64 (for the tensor-core forms the wide kernel's row work
+// runs in double-float on the FP32 pipe, see update_wide_body).  Input: the S split-K partials of the
 // concurrent MTTKRP Mbar_n (S x I_n x C: FP64, FP32 or FP32 pairs by form); the
 // block sums the partials of its own rows in split order, with the steps of the
 // reduction kernels, so Mbar_n is the same FP64 value they would give.
@@ -74,6 +75,59 @@ __device__ __forceinline__ void split_f32_pair(double u, float& hi, float& lo) {
   }
   const float mag = __uint2float_rn(r) * __uint_as_float((uint32_t)(e - 52 + 127) << 23);   // exact
   lo = (up != (sign != 0u)) ? -mag : mag;   // u - hi has u's sign when hi was rounded down
+}
+
+// ---- double-float arithmetic for the tensor-core forms' row work ----------------
+// A value is an unevaluated pair h + l of FP32 numbers with |l| <= ulp(h)/2 (about
+// 48 significant bits).  Sums use Knuth's TwoSum on the leading parts, products
+// the FMA-exact product of the leading parts plus the cross terms; each result is
+// renormalised with a fast two-sum.  Relative error of one operation about
+// 2^-44, far below the tensor-core forms' MTTKRP error (>= 2e-9).  All steps
+// are explicit round-to-nearest intrinsics, so no contraction or reassociation
+// changes them.
+struct dfl {
+  float h, l;
+};
+
+__device__ __forceinline__ dfl dfl_of(double x) {
+  dfl r;
+  split_f32_pair(x, r.h, r.l);
+  return r;
+}
+
+__device__ __forceinline__ double dfl_to_double(dfl a) { return df_to_double(a.h, a.l); }
+
+__device__ __forceinline__ dfl dfl_renorm(float s, float t) {
+  const float h = __fadd_rn(s, t);
+  return dfl{h, __fsub_rn(t, __fsub_rn(h, s))};
+}
+
+__device__ __forceinline__ dfl dfl_add(dfl a, dfl b) {
+  const float s = __fadd_rn(a.h, b.h);
+  const float bb = __fsub_rn(s, a.h);
+  const float e = __fadd_rn(__fsub_rn(a.h, __fsub_rn(s, bb)), __fsub_rn(b.h, bb));
+  return dfl_renorm(s, __fadd_rn(__fadd_rn(e, a.l), b.l));
+}
+
+__device__ __forceinline__ dfl dfl_mul(dfl a, dfl b) {
+  const float p = __fmul_rn(a.h, b.h);
+  float e = __fmaf_rn(a.h, b.h, -p);
+  e = __fmaf_rn(a.h, b.l, e);
+  e = __fmaf_rn(a.l, b.h, e);
+  return dfl_renorm(p, e);
+}
+
+// c - a * b
+__device__ __forceinline__ dfl dfl_sub_mul(dfl c, dfl a, dfl b) {
+  const dfl p = dfl_mul(a, b);
+  return dfl_add(c, dfl{-p.h, -p.l});
+}
+
+// c + a * b
+__device__ __forceinline__ dfl dfl_add_mul(dfl c, dfl a, dfl b) { return dfl_add(c, dfl_mul(a, b)); }
+
+__device__ __forceinline__ dfl dfl_shfl_xor(dfl a, int o) {
+  return dfl{__shfl_xor_sync(0xffffffffu, a.h, o), __shfl_xor_sync(0xffffffffu, a.l, o)};
 }
 
 // RMAX bounds the rank of every block; FIXED means every block has exactly RMAX
@@ -424,7 +478,11 @@ __host__ __device__ inline int wide_row_threads(int64_t I) {
 
 // Block g of one problem; the CTA has at least 32 + wide_row_threads(a.I)
 // threads; the ones beyond take no rows but meet every barrier.
-template <int RMAX, bool FIXED>
+// DF (tensor-core forms): the split-K sums stay FP32 pairs, and the row solves,
+// the Gram and fit sums and their reduction run in double-float arithmetic on the
+// FP32 pipe; the R x R Hadamard, its Cholesky factor, the normalisation and the
+// error stay FP64.  Without DF (the FP64 form) every step is FP64.
+template <int RMAX, bool FIXED, bool DF>
 __device__ __forceinline__ void update_wide_body(const UpdateArgs& a, int g, double* X) {
   constexpr int NP = RMAX * (RMAX + 1) / 2;   // Gram entries (upper triangle), then the fit term
   constexpr int NPAD = wide_npad(RMAX);
@@ -448,6 +506,8 @@ __device__ __forceinline__ void update_wide_body(const UpdateArgs& a, int g, dou
   __shared__ double L[RMAX][RMAX + 1];
   __shared__ double Hc[RMAX * RMAX];
   __shared__ double invd[RMAX];
+  __shared__ dfl Lp[DF ? RMAX : 1][RMAX + 1];   // DF: L and 1 / diag(L) as pairs
+  __shared__ dfl invdp[DF ? RMAX : 1];
   __shared__ double scale[RMAX];
   __shared__ double wsum[(kWideRows + 32) / 32][NPAD];
   __shared__ double tot[NPAD];
@@ -485,6 +545,13 @@ __device__ __forceinline__ void update_wide_body(const UpdateArgs& a, int g, dou
         L[i][j] = v * invd[j];
       }
       __syncwarp();
+    }
+    if constexpr (DF) {
+      for (int p = lane; p < R * R; p += 32) {
+        const int r = p / R, k = p % R;
+        if (k < r) Lp[r][k] = dfl_of(L[r][k]);
+        if (k == r) invdp[r] = dfl_of(invd[r]);
+      }
     }
   } else {
     // the block's rows of Mbar_n: each element the sum of its S partials in split
@@ -541,12 +608,33 @@ __device__ __forceinline__ void update_wide_body(const UpdateArgs& a, int g, dou
               }
             }
         }
+        if constexpr (DF) {
+          // the pair itself (renormalised), no FP64 conversion
+          float2* X2 = reinterpret_cast<float2*>(X);
+#pragma unroll
+          for (int r = 0; r < RMAX; ++r)
+            if (r < R) {
+              const dfl m = dfl_renorm(hi[r], lo[r]);
+              X2[i * R + r] = make_float2(m.h, m.l);
+            }
+          continue;
+        }
 #pragma unroll
         for (int r = 0; r < RMAX; ++r) v[r] = df_to_double(hi[r], lo[r]);
       }
+      if constexpr (DF) {
+        float2* X2 = reinterpret_cast<float2*>(X);
 #pragma unroll
-      for (int r = 0; r < RMAX; ++r)
-        if (r < R) X[i * R + r] = v[r];
+        for (int r = 0; r < RMAX; ++r)
+          if (r < R) {
+            const dfl m = dfl_of(v[r]);
+            X2[i * R + r] = make_float2(m.h, m.l);
+          }
+      } else {
+#pragma unroll
+        for (int r = 0; r < RMAX; ++r)
+          if (r < R) X[i * R + r] = v[r];
+      }
     }
   }
   __syncthreads();
@@ -562,69 +650,142 @@ __device__ __forceinline__ void update_wide_body(const UpdateArgs& a, int g, dou
   double acc[NPAD];
 #pragma unroll
   for (int p = 0; p < NPAD; ++p) acc[p] = 0.0;
-  if (rows) {
-    for (int64_t i = tid - 32; i < I; i += RT) {
-      double x[RMAX], m[RMAX];
+  if constexpr (DF) {
+    dfl accp[NPAD];
 #pragma unroll
-      for (int r = 0; r < RMAX; ++r) m[r] = (r < R) ? X[i * R + r] : 0.0;
-      if (a.n == a.n_hat && left_out(a.bm, g, i)) {
-#pragma unroll
-        for (int r = 0; r < RMAX; ++r) x[r] = 0.0;
-      } else {
+    for (int p = 0; p < NPAD; ++p) accp[p] = dfl{0.f, 0.f};
+    float2* X2 = reinterpret_cast<float2*>(X);
+    if (rows) {
+      for (int64_t i = tid - 32; i < I; i += RT) {
+        dfl x[RMAX], m[RMAX];
 #pragma unroll
         for (int r = 0; r < RMAX; ++r) {
-          if (r < R) {
-            double v = m[r];
+          const float2 t = (r < R) ? X2[i * R + r] : make_float2(0.f, 0.f);
+          m[r] = dfl{t.x, t.y};
+          x[r] = dfl{0.f, 0.f};
+        }
+        if (!(a.n == a.n_hat && left_out(a.bm, g, i))) {
 #pragma unroll
-            for (int k = 0; k < r; ++k) v -= L[r][k] * x[k];
-            x[r] = v * invd[r];
-          } else {
-            x[r] = 0.0;
+          for (int r = 0; r < RMAX; ++r) {
+            if (r < R) {
+              dfl v = m[r];
+#pragma unroll
+              for (int k = 0; k < r; ++k) v = dfl_sub_mul(v, Lp[r][k], x[k]);
+              x[r] = dfl_mul(v, invdp[r]);
+            }
+          }
+#pragma unroll
+          for (int r = RMAX - 1; r >= 0; --r) {
+            if (r < R) {
+              dfl v = x[r];
+#pragma unroll
+              for (int k = r + 1; k < RMAX; ++k)
+                if (k < R) v = dfl_sub_mul(v, Lp[k][r], x[k]);
+              x[r] = dfl_mul(v, invdp[r]);
+            }
           }
         }
 #pragma unroll
-        for (int r = RMAX - 1; r >= 0; --r) {
-          if (r < R) {
-            double v = x[r];
+        for (int r = 0; r < RMAX; ++r)
+          if (r < R) X2[i * R + r] = make_float2(x[r].h, x[r].l);
+        int p = 0;
 #pragma unroll
-            for (int k = r + 1; k < RMAX; ++k)
-              if (k < R) v -= L[k][r] * x[k];
-            x[r] = v * invd[r];
-          }
+        for (int r0 = 0; r0 < RMAX; ++r0)
+#pragma unroll
+          for (int r1 = r0; r1 < RMAX; ++r1) accp[p] = dfl_add_mul(accp[p], x[r0], x[r1]), ++p;   // zero beyond R
+        if (last) {
+#pragma unroll
+          for (int r = 0; r < RMAX; ++r) accp[NP] = dfl_add_mul(accp[NP], x[r], m[r]);
         }
-      }
-#pragma unroll
-      for (int r = 0; r < RMAX; ++r)
-        if (r < R) X[i * R + r] = x[r];
-      int p = 0;
-#pragma unroll
-      for (int r0 = 0; r0 < RMAX; ++r0)
-#pragma unroll
-        for (int r1 = r0; r1 < RMAX; ++r1) acc[p] = fma(x[r0], x[r1], acc[p]), ++p;   // zero beyond R
-      if (last) {
-#pragma unroll
-        for (int r = 0; r < RMAX; ++r) acc[NP] = fma(x[r], m[r], acc[NP]);
       }
     }
-  }
-  // reduce-scatter across the warp: at the step with lane offset o a lane keeps
-  // the half of its values that its bit o selects and adds its partner's copy
+    // reduce-scatter as below, on the pairs
 #pragma unroll
-  for (int st = 0; st < 5; ++st) {
-    const int o = 16 >> st;
-    const bool up = (lane & o) != 0;
-    const int half = NPAD >> (st + 1);
-    if (half >= 1) {
+    for (int st = 0; st < 5; ++st) {
+      const int o = 16 >> st;
+      const bool up = (lane & o) != 0;
+      const int half = NPAD >> (st + 1);
+      if (half >= 1) {
 #pragma unroll
-      for (int j = 0; j < NPAD / 2; ++j) {
-        if (j < half) {
-          const double send = up ? acc[j] : acc[half + j];
-          const double keep = up ? acc[half + j] : acc[j];
-          acc[j] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+        for (int jj = 0; jj < NPAD / 2; ++jj) {
+          if (jj < half) {
+            const dfl send = up ? accp[jj] : accp[half + jj];
+            const dfl keep = up ? accp[half + jj] : accp[jj];
+            accp[jj] = dfl_add(keep, dfl_shfl_xor(send, o));
+          }
+        }
+      } else {
+        accp[0] = dfl_add(accp[0], dfl_shfl_xor(accp[0], o));
+      }
+    }
+    constexpr int KEEPP = NPAD >= 32 ? NPAD / 32 : 1;
+#pragma unroll
+    for (int jj = 0; jj < KEEPP; ++jj) acc[jj] = dfl_to_double(accp[jj]);
+  } else {
+    if (rows) {
+      for (int64_t i = tid - 32; i < I; i += RT) {
+        double x[RMAX], m[RMAX];
+#pragma unroll
+        for (int r = 0; r < RMAX; ++r) m[r] = (r < R) ? X[i * R + r] : 0.0;
+        if (a.n == a.n_hat && left_out(a.bm, g, i)) {
+#pragma unroll
+          for (int r = 0; r < RMAX; ++r) x[r] = 0.0;
+        } else {
+#pragma unroll
+          for (int r = 0; r < RMAX; ++r) {
+            if (r < R) {
+              double v = m[r];
+#pragma unroll
+              for (int k = 0; k < r; ++k) v -= L[r][k] * x[k];
+              x[r] = v * invd[r];
+            } else {
+              x[r] = 0.0;
+            }
+          }
+#pragma unroll
+          for (int r = RMAX - 1; r >= 0; --r) {
+            if (r < R) {
+              double v = x[r];
+#pragma unroll
+              for (int k = r + 1; k < RMAX; ++k)
+                if (k < R) v -= L[k][r] * x[k];
+              x[r] = v * invd[r];
+            }
+          }
+        }
+#pragma unroll
+        for (int r = 0; r < RMAX; ++r)
+          if (r < R) X[i * R + r] = x[r];
+        int p = 0;
+#pragma unroll
+        for (int r0 = 0; r0 < RMAX; ++r0)
+#pragma unroll
+          for (int r1 = r0; r1 < RMAX; ++r1) acc[p] = fma(x[r0], x[r1], acc[p]), ++p;   // zero beyond R
+        if (last) {
+#pragma unroll
+          for (int r = 0; r < RMAX; ++r) acc[NP] = fma(x[r], m[r], acc[NP]);
         }
       }
-    } else {
-      acc[0] = acc[0] + __shfl_xor_sync(0xffffffffu, acc[0], o);
+    }
+    // reduce-scatter across the warp: at the step with lane offset o a lane keeps
+    // the half of its values that its bit o selects and adds its partner's copy
+#pragma unroll
+    for (int st = 0; st < 5; ++st) {
+      const int o = 16 >> st;
+      const bool up = (lane & o) != 0;
+      const int half = NPAD >> (st + 1);
+      if (half >= 1) {
+#pragma unroll
+        for (int j = 0; j < NPAD / 2; ++j) {
+          if (j < half) {
+            const double send = up ? acc[j] : acc[half + j];
+            const double keep = up ? acc[half + j] : acc[j];
+            acc[j] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+          }
+        }
+      } else {
+        acc[0] = acc[0] + __shfl_xor_sync(0xffffffffu, acc[0], o);
+      }
     }
   }
   {
@@ -675,7 +836,14 @@ __device__ __forceinline__ void update_wide_body(const UpdateArgs& a, int g, dou
 #pragma unroll
       for (int r = 0; r < RMAX; ++r) {
         if (r < R) {
-          const double x = norm ? X[i * R + r] * scale[r] : X[i * R + r];
+          double x;
+          if constexpr (DF) {
+            const float2 t = reinterpret_cast<const float2*>(X)[i * R + r];
+            const dfl xp = norm ? dfl_mul(dfl{t.x, t.y}, dfl_of(scale[r])) : dfl{t.x, t.y};
+            x = dfl_to_double(xp);
+          } else {
+            x = norm ? X[i * R + r] * scale[r] : X[i * R + r];
+          }
           a.U[i * a.C + off + r] = x;
           if (a.UT != nullptr) {
             float hi, lo;
@@ -723,10 +891,10 @@ __device__ __forceinline__ void update_wide_body(const UpdateArgs& a, int g, dou
   a.loss_prev[g] = e;
 }
 
-template <int RMAX, bool FIXED>
+template <int RMAX, bool FIXED, bool DF>
 __global__ void __launch_bounds__(kWideRows + 32, 1) update_wide_kernel(UpdateArgs a) {
   extern __shared__ double X[];
-  update_wide_body<RMAX, FIXED>(a, blockIdx.x, X);
+  update_wide_body<RMAX, FIXED, DF>(a, blockIdx.x, X);
 }
 
 // Block x of a grouped launch belongs to problem b with first[b] <= x < first[b + 1].
@@ -745,7 +913,7 @@ __device__ __forceinline__ void load_args(UpdateArgs& sa, const UpdateArgs* args
   for (int i = threadIdx.x; i < (int)(sizeof(UpdateArgs) / 4); i += blockDim.x) dst[i] = __ldg(src + i);
 }
 
-template <int RMAX, bool FIXED>
+template <int RMAX, bool FIXED, bool DF>
 __global__ void __launch_bounds__(kWideRows + 32, 1) update_wide_grouped_kernel(const UpdateArgs* __restrict__ args,
                                                                                const int* __restrict__ first,
                                                                                int nprob) {
@@ -754,7 +922,7 @@ __global__ void __launch_bounds__(kWideRows + 32, 1) update_wide_grouped_kernel(
   const int b = group_problem_u(first, nprob, (int)blockIdx.x);
   load_args(sa, args, b);
   __syncthreads();
-  update_wide_body<RMAX, FIXED>(sa, (int)blockIdx.x - __ldg(first + b), X);
+  update_wide_body<RMAX, FIXED, DF>(sa, (int)blockIdx.x - __ldg(first + b), X);
 }
 
 template <int RMAX, bool FIXED>
@@ -769,16 +937,28 @@ __global__ void __launch_bounds__(NT, 2) update_fused_grouped_kernel(const Updat
   update_fused_body<RMAX, FIXED>(sa, (int)blockIdx.x - __ldg(first + b), X);
 }
 
+template <int RM, bool F, bool DF>
+cudaError_t raise_wide_smem(size_t smem) {
+  cudaFuncAttributes fa;
+  const cudaError_t e = cudaFuncGetAttributes(&fa, update_wide_kernel<RM, F, DF>);
+  if (e != cudaSuccess) return e;
+  if ((size_t)fa.maxDynamicSharedSizeBytes >= smem) return cudaSuccess;
+  return cudaFuncSetAttribute(update_wide_kernel<RM, F, DF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+// The tensor-core forms (the update also writes their FP32 factor copies) take
+// the double-float row work.
 template <int RM, bool F>
 cudaError_t run_wide(const UpdateArgs* a, size_t smem, cudaStream_t s, bool prepare) {
   if (prepare) {
-    cudaFuncAttributes fa;
-    const cudaError_t e = cudaFuncGetAttributes(&fa, update_wide_kernel<RM, F>);
-    if (e != cudaSuccess) return e;
-    if ((size_t)fa.maxDynamicSharedSizeBytes >= smem) return cudaSuccess;
-    return cudaFuncSetAttribute(update_wide_kernel<RM, F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const cudaError_t e = raise_wide_smem<RM, F, false>(smem);
+    return e != cudaSuccess ? e : raise_wide_smem<RM, F, true>(smem);
   }
-  update_wide_kernel<RM, F><<<a->K, (unsigned)(wide_row_threads(a->I) + 32), smem, s>>>(*a);
+  const unsigned threads = (unsigned)(wide_row_threads(a->I) + 32);
+  if (a->UT != nullptr)
+    update_wide_kernel<RM, F, true><<<a->K, threads, smem, s>>>(*a);
+  else
+    update_wide_kernel<RM, F, false><<<a->K, threads, smem, s>>>(*a);
   return cudaGetLastError();
 }
 
@@ -841,20 +1021,21 @@ cudaError_t run_grouped(KF kernel, bool prepare, unsigned threads, const UpdateA
   return cudaGetLastError();
 }
 
-// The same instance that dispatch_fused picks for (Rmax, uniform), grouped;
+// The same instance that dispatch_fused picks for (Rmax, uniform), grouped (every
+// problem of a grouped batch runs a tensor-core form: the double-float row work);
 // threads: the largest CTA that a problem of the group takes on its own.
 cudaError_t dispatch_grouped(bool prepare, const UpdateArgs* args, const int* first, int nprob, int total,
                              int threads, int Rmax, bool uniform, size_t smem, cudaStream_t s) {
   const unsigned tw = (unsigned)threads;
   if (uniform) {
     switch (Rmax) {
-      case 1: return run_grouped(update_wide_grouped_kernel<1, true>, prepare, tw, args, first, nprob, total, smem, s);
-      case 2: return run_grouped(update_wide_grouped_kernel<2, true>, prepare, tw, args, first, nprob, total, smem, s);
-      case 3: return run_grouped(update_wide_grouped_kernel<3, true>, prepare, tw, args, first, nprob, total, smem, s);
-      case 4: return run_grouped(update_wide_grouped_kernel<4, true>, prepare, tw, args, first, nprob, total, smem, s);
-      case 5: return run_grouped(update_wide_grouped_kernel<5, true>, prepare, tw, args, first, nprob, total, smem, s);
-      case 6: return run_grouped(update_wide_grouped_kernel<6, true>, prepare, tw, args, first, nprob, total, smem, s);
-      case 7: return run_grouped(update_wide_grouped_kernel<7, true>, prepare, tw, args, first, nprob, total, smem, s);
+      case 1: return run_grouped(update_wide_grouped_kernel<1, true, true>, prepare, tw, args, first, nprob, total, smem, s);
+      case 2: return run_grouped(update_wide_grouped_kernel<2, true, true>, prepare, tw, args, first, nprob, total, smem, s);
+      case 3: return run_grouped(update_wide_grouped_kernel<3, true, true>, prepare, tw, args, first, nprob, total, smem, s);
+      case 4: return run_grouped(update_wide_grouped_kernel<4, true, true>, prepare, tw, args, first, nprob, total, smem, s);
+      case 5: return run_grouped(update_wide_grouped_kernel<5, true, true>, prepare, tw, args, first, nprob, total, smem, s);
+      case 6: return run_grouped(update_wide_grouped_kernel<6, true, true>, prepare, tw, args, first, nprob, total, smem, s);
+      case 7: return run_grouped(update_wide_grouped_kernel<7, true, true>, prepare, tw, args, first, nprob, total, smem, s);
       case 8:
         return run_grouped(update_fused_grouped_kernel<8, true>, prepare, NT, args, first, nprob, total, smem, s);
       default: break;
