@@ -1188,6 +1188,19 @@ __global__ void __launch_bounds__(kThreads, 1) mttkrp_tts_kernel(const TcArgs a)
         const uint64_t bd0 = ad0 + (uint64_t)(a_stage >> 4);
         issue_stage<Cfg, VAR, false, ROW / 32>(td, ad0, bd0, L, b16, idesc, kin == 0);
         tc_commit(&empty[st]);
+        // the next k-step of the same o in the next stage of the same pass, in the
+        // same trip through the loop (each stage still released by its own commit)
+        if (kin + 1 < nkt_a && sp + 1 < Sh && it + 1 < nke) {
+          ok = wait_bounded(&full[st + 1], ph, abort_flag, a.err, 2);
+          if (!ok) break;
+          tc_fence_after();
+          const uint64_t st16 = (uint64_t)(stage_bytes >> 4);
+          issue_stage<Cfg, VAR, false, ROW / 32>(td, ad0 + st16, bd0 + st16, L, b16, idesc, false);
+          tc_commit(&empty[st + 1]);
+          ++it;
+          ++kin;
+          ++sp;
+        }
         if (++kin == nkt_a) {
           tc_commit(&accum[b]);   // o j complete in set b
           kin = 0;
