@@ -1026,6 +1026,9 @@ __global__ void slice_a_kernel(const float* __restrict__ UT, const float* __rest
   }
 }
 
+// k-steps issued per trip through the two-step kernel's issue loop at most
+constexpr int kTtsUnroll = 4;
+
 // VAR: the B parts stacked per MMA (4, 2 or 1; from the plan's stack), fixed at
 // compile time: a runtime switch over the variants costs the issuing lane about
 // 50 cycles per stage, where a stage has ~700 cycles of tensor work.
@@ -1188,18 +1191,21 @@ __global__ void __launch_bounds__(kThreads, 1) mttkrp_tts_kernel(const TcArgs a)
         const uint64_t bd0 = ad0 + (uint64_t)(a_stage >> 4);
         issue_stage<Cfg, VAR, false, ROW / 32>(td, ad0, bd0, L, b16, idesc, kin == 0);
         tc_commit(&empty[st]);
-        // the next k-step of the same o in the next stage of the same pass, in the
-        // same trip through the loop (each stage still released by its own commit)
-        if (kin + 1 < nkt_a && sp + 1 < Sh && it + 1 < nke) {
-          ok = wait_bounded(&full[st + 1], ph, abort_flag, a.err, 2);
-          if (!ok) break;
-          tc_fence_after();
-          const uint64_t st16 = (uint64_t)(stage_bytes >> 4);
-          issue_stage<Cfg, VAR, false, ROW / 32>(td, ad0 + st16, bd0 + st16, L, b16, idesc, false);
-          tc_commit(&empty[st + 1]);
+        // the following k-steps of the same o in the following stages of the same
+        // pass, up to the whole ring, in the same trip through the loop (each stage
+        // still released by its own commit right after its MMAs)
+#pragma unroll
+        for (int u = 1; u < kTtsUnroll; ++u) {
+          if (!(kin + 1 < nkt_a && sp + 1 < Sh && it + 1 < nke)) break;
           ++it;
           ++kin;
           ++sp;
+          ok = wait_bounded(&full[st + u], ph, abort_flag, a.err, 2);
+          if (!ok) break;
+          tc_fence_after();
+          const uint64_t stu = (uint64_t)(((uint32_t)u * stage_bytes) >> 4);
+          issue_stage<Cfg, VAR, false, ROW / 32>(td, ad0 + stu, bd0 + stu, L, b16, idesc, false);
+          tc_commit(&empty[st + u]);
         }
         if (++kin == nkt_a) {
           tc_commit(&accum[b]);   // o j complete in set b
