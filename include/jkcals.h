@@ -341,6 +341,23 @@ void jkcals_batch_destroy(jkcals_batch_t b);
  */
 jkcals_status jkcals_loss_history(jkcals_t h, int nsweeps, double* losses);
 
+/*
+ * Self-test of the bounded waits that every pipelined kernel relies on (a
+ * health check; no counterpart in the paper).  One CTA on the current device:
+ * one thread waits on a barrier phase that nothing completes, with a limit of
+ * limit_ms (0 < limit_ms <= 100); it must give up, raise the CTA's abort flag
+ * and record its code (3) in the error word.  A thread of another warp,
+ * blocked in a wait with a limit 64 times longer, must leave through the abort
+ * flag.  No trap and no fault: the kernel returns and the context stays
+ * usable.
+ *  code           the error word the kernel recorded (3 when the wait expired as designed)
+ *  left_after_ms  time from the start until the second thread left its wait (about limit_ms)
+ * Returns JKCALS_OK after the kernel completed and neither wait claimed a
+ * completion that never happened; JKCALS_ERR_STATE if one did; JKCALS_ERR_ARG
+ * or JKCALS_ERR_CUDA otherwise.  Synchronises the device.
+ */
+jkcals_status jkcals_selftest_bounded_wait(double limit_ms, int* code, double* left_after_ms);
+
 /* Block until the handle's stream is idle. */
 jkcals_status jkcals_sync(jkcals_t h);
 

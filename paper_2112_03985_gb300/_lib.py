@@ -55,6 +55,7 @@ SIGNATURES = {
     "jkcals_batch_sync": (ct.c_int, [P]),
     "jkcals_batch_destroy": (None, [P]),
     "jkcals_sync": (ct.c_int, [P]),
+    "jkcals_selftest_bounded_wait": (ct.c_int, [ct.c_double, I32P, ct.POINTER(ct.c_double)]),
     "jkcals_mttkrp_f64_noalloc": (ct.c_int, [ct.c_int, I64P, ct.c_int, P, PP, ct.c_int, P, P]),
     "jkcals_last_error": (ct.c_char_p, []),
     "jkcals_version": (ct.c_char_p, []),

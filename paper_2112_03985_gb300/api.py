@@ -358,6 +358,16 @@ def _loss_function():
     return _LOSS_FN
 
 
+def selftest_bounded_wait(limit_ms: float = 20.0):
+    """jkcals_selftest_bounded_wait: runs the bounded-wait self-test on the current
+    device; returns (status, error code recorded, ms until the second waiter left)."""
+    lib = L.load()
+    code = ct.c_int32(0)
+    left = ct.c_double(0.0)
+    st = lib.jkcals_selftest_bounded_wait(float(limit_ms), ct.byref(code), ct.byref(left))
+    return int(st), int(code.value), float(left.value)
+
+
 def plan_query(dims: Sequence[int], ranks: Sequence[int], precision: str = "fp64", splits: int = 0,
                num_sms: int = 152):
     """The per-mode plan jkcals_create would make (host only, no device): kernel ('fp64',

@@ -87,20 +87,26 @@ __device__ __forceinline__ uint64_t global_ns() {
 }
 
 // Bounded wait for the phase with the given parity.  Returns false if this
-// CTA aborted (another role timed out) or the limit expired (then it aborts).
-__device__ __forceinline__ bool wait_bounded(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
-                                             int* err, int code) {
+// CTA aborted (another role timed out) or the limit expired (then it raises the
+// CTA's abort flag, records its code in the error word and returns).
+__device__ __forceinline__ bool wait_bounded_ns(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int* err,
+                                                int code, uint64_t limit_ns) {
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = global_ns();
   while (true) {
     if (mbar_try_wait(bar, parity)) return true;
     if (*abort_flag) return false;
-    if (global_ns() - t0 > kWaitLimitNs) {
+    if (global_ns() - t0 > limit_ns) {
       *abort_flag = 1;
       atomicExch(err, code);
       return false;
     }
   }
+}
+
+__device__ __forceinline__ bool wait_bounded(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
+                                             int* err, int code) {
+  return wait_bounded_ns(bar, parity, abort_flag, err, code, kWaitLimitNs);
 }
 
 // Bounded wait for threads that have nothing else to do: each try_wait may
