@@ -1683,6 +1683,7 @@ jkcals_status capture_grouped(jkcals_batch_ctx* b, cudaGraph_t* graph) {
   struct UpdClass {
     int Rmax;
     bool uniform;
+    bool df;   // wide_update_double_float of the class's problems (this mode)
     int threads = 0;
     size_t smem = 0;
     std::vector<UpdateArgs> args;
@@ -1696,10 +1697,11 @@ jkcals_status capture_grouped(jkcals_batch_ctx* b, cudaGraph_t* graph) {
     for (jkcals_ctx* h : b->hs) {
       if (!h->plan[n].upd.fused) continue;
       UpdClass* c = nullptr;
+      const bool df = wide_update_double_float(h->tc, h->dims[n]);
       for (UpdClass& u : upd[n])
-        if (u.Rmax == h->Rmax && u.uniform == h->uniform_rank) c = &u;
+        if (u.Rmax == h->Rmax && u.uniform == h->uniform_rank && u.df == df) c = &u;
       if (c == nullptr) {
-        upd[n].push_back(UpdClass{h->Rmax, h->uniform_rank});
+        upd[n].push_back(UpdClass{h->Rmax, h->uniform_rank, df});
         c = &upd[n].back();
       }
       c->args.push_back(update_args(h, n, h->part, part_kind(h), mode_splits(h, n)));
@@ -1714,7 +1716,7 @@ jkcals_status capture_grouped(jkcals_batch_ctx* b, cudaGraph_t* graph) {
       JK_TRY(batch_upload(b, &df, c.first.data(), sizeof(int) * c.first.size()));
       c.dargs = static_cast<const UpdateArgs*>(da);
       c.dfirst = static_cast<const int*>(df);
-      const cudaError_t e = prepare_update_grouped(c.threads, c.Rmax, c.uniform, c.smem);
+      const cudaError_t e = prepare_update_grouped(c.threads, c.Rmax, c.uniform, c.df, c.smem);
       if (e != cudaSuccess) return fail(JKCALS_ERR_CUDA, std::string("grouped update attributes: ") + cudaGetErrorString(e));
     }
   }
@@ -1766,7 +1768,7 @@ jkcals_status capture_grouped(jkcals_batch_ctx* b, cudaGraph_t* graph) {
       const UpdClass& c = upd[n][ci];
       if (st != JKCALS_OK) break;
       e = launch_update_grouped(c.dargs, c.dfirst, (int)c.args.size(), c.first.back(), c.threads, c.Rmax, c.uniform,
-                                c.smem, side[ci]);
+                                c.df, c.smem, side[ci]);
       if (e != cudaSuccess)
         st = fail(JKCALS_ERR_CUDA, std::string("grouped update (mode ") + std::to_string(n) + ", rank class " +
                                        std::to_string(c.Rmax) + (c.uniform ? " uniform" : " mixed") + ", " +

@@ -339,10 +339,16 @@ cudaError_t launch_update_fused(const UpdateArgs& a, size_t smem, int Rmax, bool
 // update_fused_smem.  Each block's arithmetic is that of launch_update_fused
 // for its problem.
 int update_fused_threads(int64_t I, int Rmax, bool uniform);
+// Whether the wide update of a tensor-core form (the update writes FP32 factor
+// copies) runs its row work in double-float: on modes of more than 128 rows,
+// where a row thread solves two rows and FP64 throughput bounds the block; with
+// one row per thread the chain's latency bounds it and FP64's shorter chain wins.
+inline bool wide_update_double_float(bool tc, int64_t I) { return tc && I > 128; }
 std::string grouped_update_attrs();   // diagnostics of the last grouped update launch
-cudaError_t prepare_update_grouped(int threads, int Rmax, bool uniform, size_t smem);
+// df: the classes' wide_update_double_float (one value per grouped launch)
+cudaError_t prepare_update_grouped(int threads, int Rmax, bool uniform, bool df, size_t smem);
 cudaError_t launch_update_grouped(const UpdateArgs* args, const int* first, int nprob, int total, int threads,
-                                  int Rmax, bool uniform, size_t smem, cudaStream_t s);
+                                  int Rmax, bool uniform, bool df, size_t smem, cudaStream_t s);
 
 cudaError_t launch_advance_sweep(int* sweep_idx, cudaStream_t s);
 cudaError_t launch_advance_sweeps(int* const* sweep_idx, int n, cudaStream_t s);   // n device counters

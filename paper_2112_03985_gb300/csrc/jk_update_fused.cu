@@ -946,8 +946,7 @@ cudaError_t raise_wide_smem(size_t smem) {
   return cudaFuncSetAttribute(update_wide_kernel<RM, F, DF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
-// The tensor-core forms (the update also writes their FP32 factor copies) take
-// the double-float row work.
+// Tensor-core forms take the double-float row work where wide_update_double_float says so.
 template <int RM, bool F>
 cudaError_t run_wide(const UpdateArgs* a, size_t smem, cudaStream_t s, bool prepare) {
   if (prepare) {
@@ -955,7 +954,7 @@ cudaError_t run_wide(const UpdateArgs* a, size_t smem, cudaStream_t s, bool prep
     return e != cudaSuccess ? e : raise_wide_smem<RM, F, true>(smem);
   }
   const unsigned threads = (unsigned)(wide_row_threads(a->I) + 32);
-  if (a->UT != nullptr)
+  if (wide_update_double_float(a->UT != nullptr, a->I))
     update_wide_kernel<RM, F, true><<<a->K, threads, smem, s>>>(*a);
   else
     update_wide_kernel<RM, F, false><<<a->K, threads, smem, s>>>(*a);
@@ -1021,21 +1020,32 @@ cudaError_t run_grouped(KF kernel, bool prepare, unsigned threads, const UpdateA
   return cudaGetLastError();
 }
 
-// The same instance that dispatch_fused picks for (Rmax, uniform), grouped (every
-// problem of a grouped batch runs a tensor-core form: the double-float row work);
-// threads: the largest CTA that a problem of the group takes on its own.
+// The same instance that dispatch_fused picks for (Rmax, uniform), grouped; df:
+// the double-float row work of the wide kernel (every problem of the launch
+// agrees on it); threads: the largest CTA that a problem of the group takes on
+// its own.
+template <bool DF>
+cudaError_t dispatch_wide_grouped(bool prepare, const UpdateArgs* args, const int* first, int nprob, int total,
+                                  unsigned tw, int Rmax, size_t smem, cudaStream_t s) {
+  switch (Rmax) {
+    case 1: return run_grouped(update_wide_grouped_kernel<1, true, DF>, prepare, tw, args, first, nprob, total, smem, s);
+    case 2: return run_grouped(update_wide_grouped_kernel<2, true, DF>, prepare, tw, args, first, nprob, total, smem, s);
+    case 3: return run_grouped(update_wide_grouped_kernel<3, true, DF>, prepare, tw, args, first, nprob, total, smem, s);
+    case 4: return run_grouped(update_wide_grouped_kernel<4, true, DF>, prepare, tw, args, first, nprob, total, smem, s);
+    case 5: return run_grouped(update_wide_grouped_kernel<5, true, DF>, prepare, tw, args, first, nprob, total, smem, s);
+    case 6: return run_grouped(update_wide_grouped_kernel<6, true, DF>, prepare, tw, args, first, nprob, total, smem, s);
+    default: return run_grouped(update_wide_grouped_kernel<7, true, DF>, prepare, tw, args, first, nprob, total, smem, s);
+  }
+}
+
 cudaError_t dispatch_grouped(bool prepare, const UpdateArgs* args, const int* first, int nprob, int total,
-                             int threads, int Rmax, bool uniform, size_t smem, cudaStream_t s) {
+                             int threads, int Rmax, bool uniform, bool df, size_t smem, cudaStream_t s) {
   const unsigned tw = (unsigned)threads;
+  if (uniform && Rmax >= 1 && Rmax <= 7)
+    return df ? dispatch_wide_grouped<true>(prepare, args, first, nprob, total, tw, Rmax, smem, s)
+              : dispatch_wide_grouped<false>(prepare, args, first, nprob, total, tw, Rmax, smem, s);
   if (uniform) {
     switch (Rmax) {
-      case 1: return run_grouped(update_wide_grouped_kernel<1, true, true>, prepare, tw, args, first, nprob, total, smem, s);
-      case 2: return run_grouped(update_wide_grouped_kernel<2, true, true>, prepare, tw, args, first, nprob, total, smem, s);
-      case 3: return run_grouped(update_wide_grouped_kernel<3, true, true>, prepare, tw, args, first, nprob, total, smem, s);
-      case 4: return run_grouped(update_wide_grouped_kernel<4, true, true>, prepare, tw, args, first, nprob, total, smem, s);
-      case 5: return run_grouped(update_wide_grouped_kernel<5, true, true>, prepare, tw, args, first, nprob, total, smem, s);
-      case 6: return run_grouped(update_wide_grouped_kernel<6, true, true>, prepare, tw, args, first, nprob, total, smem, s);
-      case 7: return run_grouped(update_wide_grouped_kernel<7, true, true>, prepare, tw, args, first, nprob, total, smem, s);
       case 8:
         return run_grouped(update_fused_grouped_kernel<8, true>, prepare, NT, args, first, nprob, total, smem, s);
       default: break;
@@ -1055,13 +1065,13 @@ int update_fused_threads(int64_t I, int Rmax, bool uniform) {
   return (uniform && Rmax <= 7) ? wide_row_threads(I) + 32 : NT;
 }
 
-cudaError_t prepare_update_grouped(int threads, int Rmax, bool uniform, size_t smem) {
-  return dispatch_grouped(true, nullptr, nullptr, 0, 0, threads, Rmax, uniform, smem, nullptr);
+cudaError_t prepare_update_grouped(int threads, int Rmax, bool uniform, bool df, size_t smem) {
+  return dispatch_grouped(true, nullptr, nullptr, 0, 0, threads, Rmax, uniform, df, smem, nullptr);
 }
 
 cudaError_t launch_update_grouped(const UpdateArgs* args, const int* first, int nprob, int total, int threads,
-                                  int Rmax, bool uniform, size_t smem, cudaStream_t s) {
-  return dispatch_grouped(false, args, first, nprob, total, threads, Rmax, uniform, smem, s);
+                                  int Rmax, bool uniform, bool df, size_t smem, cudaStream_t s) {
+  return dispatch_grouped(false, args, first, nprob, total, threads, Rmax, uniform, df, smem, s);
 }
 
 size_t update_fused_smem(int64_t I, int Rmax) { return (size_t)I * Rmax * sizeof(double); }
