@@ -137,6 +137,12 @@ void jkcals_default_options(jkcals_options* opt);
  *  opt           options or NULL for the defaults
  *  stream        cudaStream_t as void*, NULL = legacy default stream
  *
+ * Device memory comes from the library's stream-ordered memory pool of the
+ * current device (allocated on the handle's stream; the call returns after
+ * the stream is idle).  Memory freed by destroyed handles stays in that pool,
+ * up to 2 GiB per device, for the next handle; more is returned to the device
+ * at synchronisation points.  Without pool support the handle uses cudaMalloc.
+ *
  * Limits: N <= 8, R_g <= 32, prod(dims) < 2^40.
  * Errors: ARG on any invalid value, OOM, CUDA, UNSUPPORTED (limits).
  */
@@ -145,7 +151,10 @@ jkcals_status jkcals_create(jkcals_t* out, int N, const int64_t* dims, const voi
                             const int64_t* left_out_ptr, const int64_t* left_out_idx,
                             const double* const* init, const jkcals_options* opt, void* stream);
 
-/* Release every resource of the handle (NULL is ignored).  Synchronises the stream. */
+/* Release every resource of the handle (NULL is ignored): its device memory
+ * goes back to the library's pool in the order of the handle's stream.
+ * Synchronises the stream.  A batch that holds the handle must be destroyed
+ * first. */
 void jkcals_destroy(jkcals_t h);
 
 /*

@@ -6,6 +6,8 @@
 
 #include <algorithm>
 #include <cmath>
+#include <map>
+#include <mutex>
 #include <numeric>
 #include <string>
 #include <vector>
@@ -59,15 +61,44 @@ jkcals_status fail_cuda(jkcals_ctx* h, cudaError_t e, const char* what) {
     if (s_ != JKCALS_OK) return s_;          \
   } while (0)
 
+// The library's stream-ordered memory pool of a device, created on first use.
+// Handles allocate from it on their stream and free into it in stream order, so
+// creating and destroying handles neither calls cudaMalloc nor waits for the
+// device in cudaFree; up to kPoolKeepBytes of freed memory stays in the pool for
+// the next handle (more is returned to the device at synchronisation points).
+constexpr uint64_t kPoolKeepBytes = 2ull << 30;
+
+cudaMemPool_t library_pool(int device) {
+  static std::mutex mu;
+  static std::map<int, cudaMemPool_t> pools;
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = pools.find(device);
+  if (it != pools.end()) return it->second;
+  cudaMemPoolProps props{};
+  props.allocType = cudaMemAllocationTypePinned;
+  props.location.type = cudaMemLocationTypeDevice;
+  props.location.id = device;
+  cudaMemPool_t pool = nullptr;
+  if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) {
+    cudaGetLastError();
+    pool = nullptr;   // the handles of this device then use cudaMalloc / cudaFree
+  } else {
+    uint64_t keep = kPoolKeepBytes;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+  }
+  pools[device] = pool;
+  return pool;
+}
+
 jkcals_status dalloc(jkcals_ctx* h, void** p, size_t bytes) {
   *p = nullptr;
   if (bytes == 0) bytes = 16;
   if (h->opt.max_device_bytes > 0 && h->bytes_allocated + (int64_t)bytes > h->opt.max_device_bytes)
     return fail(JKCALS_ERR_OOM, "device memory cap (max_device_bytes) reached");
-  cudaError_t e = cudaMalloc(p, bytes);
+  cudaError_t e = h->pool ? cudaMallocFromPoolAsync(p, bytes, h->pool, h->stream) : cudaMalloc(p, bytes);
   if (e != cudaSuccess) {
     *p = nullptr;
-    return fail_cuda(nullptr, e, "cudaMalloc");
+    return fail_cuda(nullptr, e, h->pool ? "cudaMallocFromPoolAsync" : "cudaMalloc");
   }
   h->allocations.push_back(*p);
   h->bytes_allocated += (int64_t)bytes;
@@ -82,11 +113,19 @@ jkcals_status dalloc_t(jkcals_ctx* h, T** p, size_t count) {
   return s;
 }
 
-void dfree(jkcals_ctx* h, void* p) {
+// Frees p.  Unless only the handle's own stream used p (stream_only), first
+// waits for the device as cudaFree does: a batch on another stream may still be
+// reading it.
+void dfree(jkcals_ctx* h, void* p, bool stream_only = false) {
   if (p == nullptr) return;
   auto it = std::find(h->allocations.begin(), h->allocations.end(), p);
   if (it != h->allocations.end()) h->allocations.erase(it);
-  cudaFree(p);
+  if (!h->pool) {
+    cudaFree(p);
+    return;
+  }
+  if (!stream_only) cudaDeviceSynchronize();
+  cudaFreeAsync(p, h->stream);
 }
 
 bool is_host_pointer(const void* p) {
@@ -644,8 +683,15 @@ void destroy_impl(jkcals_ctx* h) {
     if (h->ev_start[n]) cudaEventDestroy(h->ev_start[n]);
     if (h->ev_stop[n]) cudaEventDestroy(h->ev_stop[n]);
   }
-  for (void* p : h->allocations) cudaFree(p);
+  // the handle's stream is idle (synchronised above) and no batch uses the handle any more
+  for (void* p : h->allocations) {
+    if (h->pool)
+      cudaFreeAsync(p, h->stream);
+    else
+      cudaFree(p);
+  }
   h->allocations.clear();
+  if (h->pool && h->stream) cudaStreamSynchronize(h->stream);
   if (h->stream && h->owns_stream) cudaStreamDestroy(h->stream);
   cudaSetDevice(cur);
   delete h;
@@ -717,7 +763,7 @@ jkcals_status create_impl(jkcals_ctx* h, const void* T, int T_dtype, const int32
     JK_CUDA(h, cudaMemcpyAsync(T32, T, sizeof(float) * total, cudaMemcpyDefault, st));
     JK_CUDA(h, launch_f32_to_f64(T32, Tc, total, st));
     JK_CUDA(h, cudaStreamSynchronize(st));
-    dfree(h, T32);
+    dfree(h, T32, true);
   }
   for (int n = 0; n < N; ++n) {
     JK_TRY(dalloc_t(h, &h->Tn64[n], total));
@@ -728,8 +774,8 @@ jkcals_status create_impl(jkcals_ctx* h, const void* T, int T_dtype, const int32
   JK_CUDA(h, launch_row_sumsq(h->Tn64[h->n_hat], h->dims[h->n_hat], h->J[h->n_hat], slice, st));
   JK_CUDA(h, launch_block_norms(slice, h->dims[h->n_hat], K, block_meta(h), h->d_normT2, st));
   JK_CUDA(h, cudaStreamSynchronize(st));
-  dfree(h, slice);
-  dfree(h, Tc);
+  dfree(h, slice, true);
+  dfree(h, Tc, true);
 
   // tensor-core forms: padded, precision-split, pre-tiled unfoldings replace the FP64 ones
   if (h->tc) {
@@ -764,7 +810,7 @@ jkcals_status create_impl(jkcals_ctx* h, const void* T, int T_dtype, const int32
     }
     JK_CUDA(h, cudaStreamSynchronize(st));
     for (int n = 0; n < N; ++n) {
-      dfree(h, h->Tn64[n]);
+      dfree(h, h->Tn64[n], true);
       h->Tn64[n] = nullptr;
       JK_TRY(dalloc_t(h, &h->UT[n], (size_t)h->C * h->Ipad[n]));
       JK_CUDA(h, cudaMemsetAsync(h->UT[n], 0, sizeof(float) * h->C * h->Ipad[n], st));
@@ -985,6 +1031,7 @@ jkcals_status jkcals_create(jkcals_t* out, int N, const int64_t* dims, const voi
     }
     h->owns_stream = true;
   }
+  h->pool = library_pool(h->device);
   jkcals_status s = create_impl(h, T, T_dtype, ranks, left_out_ptr, left_out_idx, init);
   if (s != JKCALS_OK) {
     std::string msg = g_last_error;

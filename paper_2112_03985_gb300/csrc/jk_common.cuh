@@ -120,6 +120,7 @@ struct jkcals_ctx {
   bool broken = false;
   int64_t bytes_allocated = 0;
   std::vector<void*> allocations;
+  cudaMemPool_t pool = nullptr;   // the library's stream-ordered pool of this device (null: cudaMalloc)
 
   std::vector<int> R, off, gram_off;
   std::vector<int64_t> lo_ptr, lo_idx;
