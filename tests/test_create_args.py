@@ -1,6 +1,7 @@
 """Argument checks of the entry points that take no handle (no GPU): jkcals_create,
-jkcals_batch_create and jkcals_mttkrp_f64_noalloc reject every invalid shape, block layout or
-option with its status and message before the device is touched."""
+jkcals_batch_create, jkcals_mttkrp_f64_noalloc and jkcals_selftest_bounded_wait reject every
+invalid shape, block layout, option or limit with its status and message before the device is
+touched."""
 import ctypes as ct
 
 import numpy as np
@@ -119,3 +120,19 @@ def test_noalloc_rejects(name, kw, status, msg):
     err = lib.jkcals_last_error().decode()
     assert st == status, (st, err)
     assert msg in err, err
+
+
+@pytest.mark.parametrize("limit_ms,code_ok,left_ok", [(0.0, True, True), (-1.0, True, True), (100.5, True, True),
+                                                      (float("nan"), True, True), (20.0, False, True),
+                                                      (20.0, True, False)])
+def test_bounded_wait_selftest_argument_checks(limit_ms, code_ok, left_ok):
+    """jkcals_selftest_bounded_wait rejects a limit outside (0, 100] ms or a missing
+    output with ERR_ARG before any CUDA call."""
+    lib = L.load()
+    code = ct.c_int32(-1)
+    left = ct.c_double(-1.0)
+    st = lib.jkcals_selftest_bounded_wait(limit_ms, ct.byref(code) if code_ok else None,
+                                          ct.byref(left) if left_ok else None)
+    assert st == ARG
+    assert "limit_ms" in lib.jkcals_last_error().decode()
+    assert code.value == -1 and left.value == -1.0   # outputs untouched
