@@ -481,6 +481,25 @@ jkcals_status reduce_into(jkcals_ctx* h, int n, double* out) {
   return JKCALS_OK;
 }
 
+// Kernels one sweep launches (enqueue_sweep's launches, counted without
+// launching): per mode the MTTKRP, the slicing of a two-step mode whose slices
+// are stale, and the fused update (or the reduction and the two-phase update's
+// three kernels); then the sweep counter.
+int count_sweep_kernels(const jkcals_ctx* h) {
+  int kernels = 0;
+  int sliced = -1;
+  for (int n = 0; n < h->N; ++n) {
+    const bool tts = h->tc && h->tcplan[n].tts;
+    if (tts) {
+      kernels += sliced == h->tcplan[n].a_mode ? 0 : 1;
+      sliced = h->tcplan[n].a_mode;
+    }
+    kernels += h->plan[n].upd.fused ? 2 : 4;
+    if (n == sliced) sliced = -1;
+  }
+  return kernels + 1;
+}
+
 jkcals_status enqueue_sweep(jkcals_ctx* h) {
   int kernels = 0;
   int sliced = -1;   // mode whose current slices At holds (two-step modes)
@@ -509,7 +528,7 @@ jkcals_status enqueue_sweep(jkcals_ctx* h) {
     if (n == sliced) sliced = -1;   // U_a changed: the slices in At are stale
   }
   JK_CUDA(h, launch_advance_sweep(h->d_sweep_idx, h->stream));
-  h->kernels_per_sweep = kernels + 1;
+  h->kernels_per_sweep = kernels + 1;   // = count_sweep_kernels(h)
   return JKCALS_OK;
 }
 
@@ -866,9 +885,7 @@ jkcals_status create_impl(jkcals_ctx* h, const void* T, int T_dtype, const int32
   for (int n = 0; n < N; ++n)
     if (h->plan[n].upd.fused) fsmem = std::max(fsmem, h->plan[n].upd.fused_smem);
   if (fsmem > 0) JK_CUDA(h, prepare_update_fused(fsmem, h->Rmax, h->uniform_rank));
-  h->kernels_per_sweep = 0;
-  for (int n = 0; n < N; ++n) h->kernels_per_sweep += h->plan[n].upd.fused ? 2 : 4;
-  h->kernels_per_sweep += 1;
+  h->kernels_per_sweep = count_sweep_kernels(h);
   JK_TRY(refresh_factor_state(h));
   if (h->opt.autotune && h->opt.splits <= 0) JK_TRY(autotune_splits(h));
   JK_CUDA(h, cudaStreamSynchronize(st));

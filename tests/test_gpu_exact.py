@@ -141,3 +141,17 @@ def test_mode_plan_reports_the_kernel_of_each_mode():
         assert p[n]["stages"] >= 2
     with api.from_workload(W.make_config(1), device="cuda:0") as h:
         assert h.mode_plan(0) == {"kernel": "fp64", "tile_rows": 64, "stages": 0, "fastest_mode": -1}
+
+
+def test_kernels_per_sweep_counts_every_launch():
+    """jkcals_sweep_info's launch count, right after create and after sweeps, is the
+    number of kernels a sweep launches.  On 300x100x50 that is 8: three MTTKRPs,
+    the one slicing launch of the two-step modes (the second reuses the first's
+    slices), three fused updates and the sweep counter."""
+    _cuda()
+    w = W.make_config(2)
+    with api.from_workload(w, precision=PREC, device="cuda") as h:
+        k0, _ = h.sweep_info()
+        h.als_sweep(2)
+        k1, _ = h.sweep_info()
+    assert k0 == k1 == 8
