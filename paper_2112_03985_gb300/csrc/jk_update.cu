@@ -48,6 +48,8 @@ __device__ __forceinline__ double load_part<float2>(const float2* p) {
   return (double)v.x + (double)v.y;
 }
 
+constexpr int kPartBatch = 8;   // split-K partials loaded together per element
+
 template <typename PT>
 __global__ void __launch_bounds__(NTA) update_phase_a(UpdateArgs a) {
   const int g = blockIdx.x, rc = blockIdx.y;
@@ -57,6 +59,7 @@ __global__ void __launch_bounds__(NTA) update_phase_a(UpdateArgs a) {
   const int go = a.bm.gram_off[g];
 
   __shared__ double Hs[kMaxRank][kMaxRank + 1];
+  __shared__ double invd[kMaxRank];   // 1 / L_jj
   __shared__ double X[NTA * kMaxRank];
   __shared__ double red[NTA];
   __shared__ int spd_ok;
@@ -83,14 +86,18 @@ __global__ void __launch_bounds__(NTA) update_phase_a(UpdateArgs a) {
           spd_ok = 0;
           d = 1.0;
         }
-        Hs[j][j] = sqrt(d);
+        // 1 / L_jj from the reciprocal square root: the column below and both
+        // substitutions multiply by it (no FP64 division on the serial paths)
+        const double rs = rsqrt(d);
+        Hs[j][j] = d * rs;
+        invd[j] = rs;
       }
       __syncwarp();
       const int i = j + 1 + lane;
       if (i < R) {
         double v = Hs[i][j];
         for (int k = 0; k < j; ++k) v -= Hs[i][k] * Hs[j][k];
-        Hs[i][j] = v / Hs[j][j];
+        Hs[i][j] = v * invd[j];
       }
       __syncwarp();
     }
@@ -116,8 +123,16 @@ __global__ void __launch_bounds__(NTA) update_phase_a(UpdateArgs a) {
     for (int r = 0; r < kMaxRank; ++r) {
       double v = 0.0;
       if (r < R) {
+        // the S partials in split order, loaded kPartBatch at a time (all in flight)
         const PT* p = part + row * a.C + off + r;
-        for (int s = 0; s < a.S; ++s) v += load_part(p + (int64_t)s * IC);
+        for (int s0 = 0; s0 < a.S; s0 += kPartBatch) {
+          double t[kPartBatch];
+#pragma unroll
+          for (int u = 0; u < kPartBatch; ++u) t[u] = s0 + u < a.S ? load_part(p + (int64_t)(s0 + u) * IC) : 0.0;
+#pragma unroll
+          for (int u = 0; u < kPartBatch; ++u)
+            if (s0 + u < a.S) v += t[u];
+        }
       }
       m[r] = v;
     }
@@ -133,7 +148,7 @@ __global__ void __launch_bounds__(NTA) update_phase_a(UpdateArgs a) {
           double v = m[r];
 #pragma unroll
           for (int k = 0; k < r; ++k) v -= Hs[r][k] * x[k];
-          x[r] = v / Hs[r][r];
+          x[r] = v * invd[r];
         } else {
           x[r] = 0.0;
         }
@@ -146,7 +161,7 @@ __global__ void __launch_bounds__(NTA) update_phase_a(UpdateArgs a) {
 #pragma unroll
           for (int k = r + 1; k < kMaxRank; ++k)
             if (k < R) v -= Hs[k][r] * x[k];
-          x[r] = v / Hs[r][r];
+          x[r] = v * invd[r];
         }
       }
     }
